@@ -1,0 +1,350 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a printed value of the paper
+(tests/golden/, each with its citation), a closed form, a special case that reduces to a library
+routine (LAPACK through numpy), an invariant, or a finite-difference derivative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import glassgen
+import oracle
+
+
+# ------------------------------------------------------------------ printed values of the paper
+def test_degrees_tables_1_3(golden):
+    """All 27 degrees of Tables 1-3: coefficients (App. A), damping (Sec. 2.3), eq. (thresh)."""
+    g = golden("degrees_tables_1_3.json")
+    rs = [0.1, 0.1 ** 0.5, 0.1 ** 0.25]
+    for case in g["cases"]:
+        for ri, r in enumerate(rs):
+            got = [oracle.select_degree(case["xi"], case["eta"], case["eps"], r, kind, kmax=7000)
+                   for kind in g["columns"]]
+            assert got == case["degrees"][ri], (case["table"], r, got)
+
+
+def test_fig3_values(golden):
+    f = golden("figures_2_3.json")["fig3"]
+    xi, eta, eps, k = f["xi"], f["eta"], f["eps"], f["degree"]
+    cj = oracle.filter_coeffs(xi, eta, eps, k, "jackson")
+    cl = oracle.filter_coeffs(xi, eta, eps, k, "lanczos")
+    half_ulp = 0.5 * 10 ** -f["printed_digits"]
+    assert abs(oracle.series_value(cj, xi - eps) - f["jackson_left"]) <= half_ulp
+    assert abs(oracle.series_value(cj, eta + eps) - f["jackson_right"]) <= half_ulp
+    assert abs(oracle.series_value(cl, xi - eps) - f["lanczos_left"]) <= 0.5e-4
+    assert abs(oracle.series_value(cl, eta + eps) - f["lanczos_right"]) <= 0.5e-4
+
+
+def test_fig2_shape(golden):
+    """The undamped series converges to p: p(xi) = p(eta) = 1, p(mid) = 1 + (eta-xi)/(2 eps) = 3,
+    p = 0 outside [xi - eps, eta + eps]; q = p' has q(xi) = 2/eps = 80 (by differencing the series)."""
+    f = golden("figures_2_3.json")["fig2"]
+    xi, eta, eps = f["xi"], f["eta"], f["eps"]
+    c = oracle.filter_coeffs(xi, eta, eps, 3000, "none")
+    assert abs(oracle.series_value(c, 0.5 * (xi + eta)) - f["p_mid"]) < 1e-3
+    assert abs(oracle.series_value(c, xi) - 1.0) < 1e-3
+    assert abs(oracle.series_value(c, eta) - 1.0) < 1e-3
+    for x in (-0.5, 0.0, xi - 2 * eps, eta + 2 * eps, 0.8):
+        assert abs(oracle.series_value(c, x)) < 1e-3
+    h = 1e-4
+    dq = (oracle.series_value(c, xi + h) - oracle.series_value(c, xi - h)) / (2 * h)
+    assert abs(dq - f["q_xi"]) < 1.0  # q has a kink at xi: the differentiated series converges like 1/k
+    # coefficients of a C^1 piecewise quadratic decay like j^-3 (Sec. 2.6)
+    j = np.arange(50, 3000)
+    assert np.max(np.abs(c[50:3000]) * j ** 3) < 10 * np.max(np.abs(c[50:100]) * j[:50] ** 3)
+
+
+def test_transform_example(golden):
+    """Eq. (transf.1) folded into Alg. 2: with coefficients e_1 the filter returns Ht x = (H - c)/d x."""
+    g = golden("transform_example.json")
+    lmin, lmax = g["lambda_min"], g["lambda_max"]
+    c, d = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    lam = np.array([p[0] for p in g["points"]])
+    H = oracle.csr_diagonal(lam)
+    y = oracle.cheb_filter(H, c, d, [0.0, 1.0], np.ones(3))[:, 0]
+    for (l0, num, den), v in zip(g["fractions"], y):
+        assert v == pytest.approx(num / den, abs=1e-15)
+
+
+def test_philox_known_answers(golden):
+    for v in golden("philox_kat.json")["vectors"]:
+        out = oracle.philox([int(x, 16) for x in v["ctr"]], [int(x, 16) for x in v["key"]])
+        assert out == [int(x, 16) for x in v["out"]]
+
+
+def test_normals_moments():
+    z = oracle.normal_block(7, 0, 200000, 1)[:, 0]
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    assert abs(np.mean(z ** 4) - 3.0) < 0.1
+
+
+# ------------------------------------------------------------------ closed forms
+def test_damping_factors():
+    for k in (1, 5, 11, 200):
+        gj = oracle.damping("jackson", k)
+        gl = oracle.damping("lanczos", k)
+        assert gj[0] == pytest.approx(1.0, abs=1e-14) and gl[0] == 1.0
+        assert np.all(np.diff(gj) <= 1e-14) and np.all(gj >= -1e-14)  # decreasing to ~0
+        assert gl[-1] == pytest.approx(math.sin(k * math.pi / (k + 1)) / (k * math.pi / (k + 1)))
+    # Jackson damping keeps a nonnegative target nonnegative (monotone approximation, Sec. 2.3)
+    xs = np.linspace(-1, 1, 801)
+    for k in (11, 60, 150):
+        c = oracle.chi_coeffs(-0.2, 0.2, k) * oracle.damping("jackson", k)
+        assert min(oracle.series_value(c, x) for x in xs) > -1e-12
+        c0 = oracle.chi_coeffs(-0.2, 0.2, k)
+        assert min(oracle.series_value(c0, x) for x in xs) < -1e-3  # the undamped series has Gibbs dips
+
+
+def test_chi_coeffs_closed_form():
+    xi, eta = -0.3, 0.4
+    c = oracle.chi_coeffs(xi, eta, 4000)
+    assert c[0] == pytest.approx((math.acos(xi) - math.acos(eta)) / math.pi, rel=1e-15)
+    assert oracle.series_value(c, 0.0) == pytest.approx(1.0, abs=2e-3)
+    assert oracle.series_value(c, 0.8) == pytest.approx(0.0, abs=2e-3)
+    assert oracle.series_value(c, xi) == pytest.approx(0.5, abs=2e-3)  # average of the jump
+
+
+def test_series_value_closed_form():
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(40)
+    for x in (-0.99, -0.3, 0.0, 0.7):
+        ref = sum(cj * math.cos(j * math.acos(x)) for j, cj in enumerate(c))
+        assert oracle.series_value(c, x) == pytest.approx(ref, abs=1e-12)
+
+
+def test_cheb_filter_diagonal_closed_form():
+    """Alg. 2 on a diagonal H: y_i = sum_j gamma_j cos(j arccos(lt_i)) x_i, lt = (lam - c)/d."""
+    rng = np.random.default_rng(1)
+    lam = np.sort(rng.uniform(0.0, 2.0, 60))
+    c, d = 1.0, 1.0
+    coef = oracle.filter_coeffs(-0.5, -0.3, 0.05, 37, "jackson")
+    X = rng.standard_normal((60, 3))
+    Y = oracle.cheb_filter(oracle.csr_diagonal(lam), c, d, coef, X)
+    lt = (lam - c) / d
+    pv = np.array([sum(g * math.cos(j * math.acos(t)) for j, g in enumerate(coef)) for t in lt])
+    assert np.allclose(Y, pv[:, None] * X, atol=1e-13, rtol=0)
+
+
+@pytest.fixture(scope="module")
+def small_glass():
+    g = glassgen.generate(60, 11)
+    H = oracle.csr_from_springs(g)
+    return g, H, H.dense()
+
+
+def test_cheb_filter_vs_eigendecomposition(small_glass):
+    """p(Ht) X = V p(lt) V^T X with LAPACK's eigendecomposition of a non-diagonal H."""
+    g, H, A = small_glass
+    w, V = np.linalg.eigh(A)
+    lmax = w[-1] * 1.01
+    c = d = lmax / 2
+    coef = oracle.filter_coeffs(-0.9, -0.7, 0.05, 50, "lanczos")
+    X = np.random.default_rng(2).standard_normal((H.n, 4))
+    Y = oracle.cheb_filter(H, c, d, coef, X)
+    lt = (w - c) / d
+    pv = np.array([oracle.series_value(coef, t) for t in lt])
+    ref = V @ (pv[:, None] * (V.T @ X))
+    assert np.allclose(Y, ref, atol=1e-12 * np.abs(ref).max(), rtol=0)
+
+
+# ------------------------------------------------------------------ model invariants
+def test_hessian_invariants(small_glass):
+    g, H, A = small_glass
+    assert np.array_equal(A, A.T)  # bitwise symmetric
+    nrm = np.linalg.norm(A, 2)
+    for ax in range(3):  # three translation modes sqrt(m_i) e_x (eq. (2))
+        v = np.zeros((g.n_atoms, 3))
+        v[:, ax] = np.sqrt(g.mass)
+        v = v.ravel()
+        assert np.linalg.norm(A @ v) <= 1e-14 * nrm * np.linalg.norm(v)
+    w = np.linalg.eigvalsh(A)
+    assert np.trace(A) == pytest.approx(w.sum(), rel=1e-12)
+    assert w[0] > -1e-13 * nrm  # positive semidefinite
+    # the quadratic form of eq. (1): q^T Delta q = sum_bonds k (r.(q_i - q_j))^2, Delta = M^1/2 H M^1/2
+    q = np.random.default_rng(3).standard_normal((g.n_atoms, 3))
+    sm = np.repeat(np.sqrt(g.mass), 3)
+    quad = (q.ravel() * sm) @ A @ (q.ravel() * sm)
+    dq = q[g.bi] - q[g.bj]
+    ref = np.sum(g.k * np.einsum("ij,ij->i", g.rhat, dq) ** 2)
+    assert quad == pytest.approx(ref, rel=1e-12)
+
+
+def test_hellmann_feynman(small_glass):
+    """d lambda / d k_e = ((v_i.r)/sqrt(m_i) - (v_j.r)/sqrt(m_j))^2 for a simple eigenpair (eq. (2))."""
+    g, H, A = small_glass
+    w, V = np.linalg.eigh(A)
+    idx = int(np.argmin(np.abs(w - 0.3 * w[-1])))
+    assert min(w[idx + 1] - w[idx], w[idx] - w[idx - 1]) > 1e-6
+    v = V[:, idx].reshape(-1, 3)
+    rng = np.random.default_rng(4)
+    for e in rng.choice(g.n_bonds, 5, replace=False):
+        i, j, r = g.bi[e], g.bj[e], g.rhat[e]
+        hf = (v[i] @ r / math.sqrt(g.mass[i]) - v[j] @ r / math.sqrt(g.mass[j])) ** 2
+        h = 1e-6 * g.k[e]
+        vals = []
+        for s in (+1, -1):
+            g2 = glassgen.Glass(**{**g.__dict__, "k": g.k.copy()})
+            g2.k[e] += s * h
+            vals.append(np.linalg.eigvalsh(oracle.csr_from_springs(g2).dense())[idx])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert fd == pytest.approx(hf, rel=1e-5, abs=1e-10)
+
+
+# ------------------------------------------------------------------ dense building blocks vs LAPACK
+def test_jacobi_vs_lapack():
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((40, 40))
+    A = B + B.T
+    w, V = oracle.jacobi_eig(A)
+    assert np.allclose(w, np.linalg.eigvalsh(A), atol=1e-12)
+    assert np.allclose(A @ V, V * w, atol=1e-11)
+    assert np.allclose(V.T @ V, np.eye(40), atol=1e-13)
+
+
+def test_householder_qr_vs_lapack():
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((300, 17))
+    Q, R = oracle.householder_qr(X)
+    assert np.allclose(Q.T @ Q, np.eye(17), atol=1e-14)
+    assert np.allclose(Q @ R, X, atol=1e-13)
+    assert np.allclose(np.tril(R, -1), 0.0)
+    _, Rl = np.linalg.qr(X)
+    assert np.allclose(np.abs(R), np.abs(Rl), atol=1e-12)
+
+
+def test_sturm_counts_vs_lapack(small_glass):
+    g, H, A = small_glass
+    w = np.linalg.eigvalsh(A)
+    d, e = oracle.tridiagonalize(A)
+    assert np.allclose(np.linalg.eigvalsh(np.diag(d) + np.diag(e, 1) + np.diag(e, -1)), w, atol=1e-13)
+    for s in np.linspace(-0.01, w[-1] * 1.1, 23):
+        if np.min(np.abs(w - s)) < 1e-9:
+            continue
+        assert oracle.count_below(d, e, s) == int(np.sum(w < s))
+
+
+def test_lanczos_upper_bound(small_glass):
+    g, H, A = small_glass
+    lmax = np.linalg.eigvalsh(A)[-1]
+    for seed in range(4):
+        th, rb, est = oracle.lanczos_lmax(H, 30, seed)
+        assert th <= lmax * (1 + 1e-12)
+        assert est >= lmax
+        assert th == pytest.approx(lmax, rel=1e-3)
+
+
+def test_count_estimator_expectation(small_glass):
+    """E[v^T psi(Ht) v] = trace(psi(Ht)) / n for normalised Gaussian v (Sec. 2.4)."""
+    g, H, A = small_glass
+    w = np.linalg.eigvalsh(A)
+    lmax = 1.01 * w[-1]
+    c = d = lmax / 2
+    a, b = 0.2 * lmax, 0.4 * lmax
+    xi, eta = (a - c) / d, (b - c) / d
+    coef = oracle.chi_coeffs(xi, eta, 100)
+    trace = sum(oracle.series_value(coef, (x - c) / d) for x in w)
+    ests = [oracle.count_estimate(H, c, d, xi, eta, 100, "none", 30, s) for s in range(20)]
+    sd = np.std(ests) / math.sqrt(len(ests))
+    assert abs(np.mean(ests) - trace) < 5 * sd + 1e-9
+    assert abs(np.mean(ests) - np.sum((w >= a) & (w <= b))) < 0.25 * np.sum((w >= a) & (w <= b)) + 5 * sd
+
+
+# ------------------------------------------------------------------ the solver
+def test_si_solve_matches_lapack():
+    """Filtered SI + Rayleigh-Ritz + locking against the exact interval eigenpairs."""
+    g = glassgen.generate(150, 2)
+    H = oracle.csr_from_springs(g)
+    A = H.dense()
+    w, V = np.linalg.eigh(A)
+    th, rb, lmax = oracle.lanczos_lmax(H, 30, 0)
+    a, b = 0.02 * lmax, 0.05 * lmax
+    sel = (w >= a) & (w <= b)
+    c = d = lmax / 2
+    xi, eta = (a - c) / d, (b - c) / d
+    eps = 0.25 * (eta - xi)
+    m = oracle.select_degree(xi, eta, eps, 0.1 ** 0.5, "jackson")
+    coef = oracle.filter_coeffs(xi, eta, eps, m, "jackson")
+    nwin = int(np.sum((w >= c + d * (xi - eps)) & (w <= c + d * (eta + eps))))
+    q = nwin + 6
+    X0 = oracle.normal_block(0, 0, H.n, q)
+    r = oracle.si_solve(H, a, b, 0.0, lmax, coef, q, X0, tol=1e-10, max_iter=60)
+    assert r.status == 0
+    assert r.lam.size == int(sel.sum())
+    assert np.allclose(r.lam, w[sel], rtol=1e-10, atol=0)
+    assert np.all(oracle.residuals(H, r.lam, r.vecs) / lmax <= 1e-10)
+    # principal angles between the computed and exact interval subspaces
+    s = np.linalg.svd(V[:, sel].T @ r.vecs, compute_uv=False)
+    assert np.min(s) > 1 - 1e-12
+
+
+def test_alg4_table1_schedule(golden):
+    """Alg. 4 as printed converges at step 7 (r = 0.1) and 13 (r = sqrt 0.1) on test case 1."""
+    g = golden("si_schedule_table1.json")
+    n = g["n"]
+    lam = -1 + (2 * np.arange(1, n + 1) - 1) / n
+    X0 = oracle.normal_block(0, 3, n, g["q"])
+    for case in (g["cases"][0], g["cases"][3]):
+        coef = oracle.filter_coeffs(g["xi"], g["eta"], g["eps"], case["degree"], case["damping"])
+        pd = np.array([oracle.series_value(coef, x) for x in lam])
+        k = oracle.si_alg4_diag(pd, g["q"], g["p"], g["n_rr"], g["tau"], X0, 40)
+        assert k == case["steps"]
+        assert k * g["q"] * case["degree"] == case["matvecs"]
+
+
+# ------------------------------------------------------------------ the adjoint
+def test_adjoint_symmetry_and_fd(small_glass):
+    g, H, A = small_glass
+    lmax = 1.01 * np.linalg.eigvalsh(A)[-1]
+    c = d = lmax / 2
+    coef = oracle.filter_coeffs(-0.9, -0.8, 0.03, 25, "jackson")
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((H.n, 2))
+    Yb = rng.standard_normal((H.n, 2))
+    Xb, vb = oracle.filter_adjoint(H, c, d, coef, X, Yb)
+    assert np.allclose(Xb, oracle.cheb_filter(H, c, d, coef, Yb), atol=1e-12 * np.abs(Xb).max())
+    rp, ci, v = H.arrays()
+
+    def loss(vals):
+        Hp = oracle.csr_from_arrays(rp, ci, vals)
+        return float(np.sum(Yb * oracle.cheb_filter(Hp, c, d, coef, X)))
+
+    for p in rng.choice(H.nnz, 12, replace=False):
+        h = 1e-6 * max(abs(v[p]), 1e-3)
+        vp, vm = v.copy(), v.copy()
+        vp[p] += h
+        vm[p] -= h
+        fd = (loss(vp) - loss(vm)) / (2 * h)
+        assert fd == pytest.approx(vb[p], rel=1e-5, abs=1e-7 * np.abs(vb).max())
+
+
+def test_chain_springs_fd(small_glass):
+    g, H, A = small_glass
+    lmax = 1.01 * np.linalg.eigvalsh(A)[-1]
+    c = d = lmax / 2
+    coef = oracle.filter_coeffs(-0.9, -0.8, 0.03, 20, "jackson")
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((H.n, 2))
+    Yb = rng.standard_normal((H.n, 2))
+    _, vb = oracle.filter_adjoint(H, c, d, coef, X, Yb)
+    kb, mb = oracle.chain_springs(H, g, vb)
+
+    def loss(gl):
+        return float(np.sum(Yb * oracle.cheb_filter(oracle.csr_from_springs(gl), c, d, coef, X)))
+
+    for e in rng.choice(g.n_bonds, 6, replace=False):
+        h = 1e-6 * g.k[e]
+        gp = glassgen.Glass(**{**g.__dict__, "k": g.k.copy()})
+        gm = glassgen.Glass(**{**g.__dict__, "k": g.k.copy()})
+        gp.k[e] += h
+        gm.k[e] -= h
+        assert (loss(gp) - loss(gm)) / (2 * h) == pytest.approx(kb[e], rel=1e-5, abs=1e-7 * np.abs(kb).max())
+    for i in rng.choice(g.n_atoms, 4, replace=False):
+        h = 1e-6 * g.mass[i]
+        gp = glassgen.Glass(**{**g.__dict__, "mass": g.mass.copy()})
+        gm = glassgen.Glass(**{**g.__dict__, "mass": g.mass.copy()})
+        gp.mass[i] += h
+        gm.mass[i] -= h
+        assert (loss(gp) - loss(gm)) / (2 * h) == pytest.approx(mb[i], rel=1e-5, abs=1e-7 * np.abs(mb).max())
