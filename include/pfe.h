@@ -1,0 +1,211 @@
+/*
+ * pfe.h -- C ABI of a single-GPU (GB300, sm_103a) polynomial-filtered interior eigensolver
+ * for mass-weighted atomistic Hessians, after Accaputo, Derlet & Arbenz, "Solving large-scale
+ * interior eigenvalue problems to investigate the vibrational properties of the boson peak
+ * regime in amorphous materials" (arXiv 1902.07041).
+ *
+ * Problem (Sec. 1, eqs. (1)-(3)): given the 3x3-block Hessian Delta of a stable atomic
+ * configuration and the masses m_i, find every eigenpair (lambda, q) of
+ *     H q = lambda q,   H_ij = Delta_ij / sqrt(m_i m_j),   lambda = omega^2,
+ * with lambda in a closed interval [a, b], ||q|| = 1, together with the residual norms
+ * (Alg. 3).  The method is the Chebyshev-filtered subspace iteration of Sec. 2.6
+ * (Alg. 2 for p_m(H) X, Alg. 4 with Rayleigh-Ritz and locking).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a pfe_status; none aborts.  On failure pfe_last_error(ctx) gives a
+ *    one-line message (thread-unsafe per context: one host thread per context at a time).
+ *  - Matrices are 3x3 block CSR ("BSR") over atoms: row_ptr[N+1] (int32, row_ptr[0] = 0),
+ *    col_idx[nnzb] (int32, ascending within a row, each row holds its diagonal block),
+ *    vals[9 * nnzb] (float64, each block row-major: vals[9p + 3r + s] = block_p(r, s)).
+ *  - Dense multivectors at the boundary are column-major n x k with a leading dimension
+ *    ld >= n, n = 3N, dof index 3i + r for atom i, Cartesian component r.
+ *  - Pointers are host pointers unless a flag or the call's description says "device".
+ *    Device pointers must come from the same CUDA device the context was created on.
+ *  - The caller keeps ownership of every buffer it passes; the library copies what it keeps.
+ *  - Streams: the context runs its work on the stream given at creation (NULL = the legacy
+ *    default stream).  Calls that take their own stream run their kernels on it.
+ */
+#ifndef PFE_H
+#define PFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfe_ctx pfe_ctx;
+
+typedef enum {
+  PFE_OK = 0,
+  PFE_E_ARG = 1,       /* invalid argument (NULL, size, index out of range, NaN/Inf input) */
+  PFE_E_NOMEM = 2,     /* host or device allocation failed */
+  PFE_E_CUDA = 3,      /* a CUDA / cuBLAS / cuSOLVER call failed; message names it */
+  PFE_E_NOTSYM = 4,    /* Delta is not symmetric: block (i,j) != block (j,i)^T beyond 1e-12 max|Delta| */
+  PFE_E_CAPACITY = 5,  /* caller buffer or subspace width too small; counts are still reported */
+  PFE_E_NOCONV = 6,    /* iteration limit reached before every interval eigenpair converged */
+  PFE_E_BREAKDOWN = 7, /* orthogonalisation broke down even after the shifted retry */
+  PFE_E_BOUND = 8,     /* lambda_max bound was violated (a Ritz value exceeded it) */
+  PFE_E_TIMEOUT = 9,   /* a bounded device-side wait gave up */
+  PFE_E_STATE = 10     /* call out of order (e.g. eigenpairs requested before a solve) */
+} pfe_status;
+
+/* flags for pfe_create and pfe_get_eigenpairs */
+#define PFE_DEVICE_PTRS 0x1u    /* array arguments are device pointers */
+#define PFE_SKIP_SYM_CHECK 0x2u /* do not verify the symmetry of Delta */
+
+/* element types of pfe_filter_apply's X and Y */
+#define PFE_F64 0 /* float64 vectors, float64 arithmetic */
+#define PFE_F32 1 /* float32 vectors, float32 arithmetic (mixed-precision filter) */
+
+/* parameter keys for pfe_set_param / pfe_get_param (values are doubles) */
+enum {
+  PFE_P_DEGREE = 1,         /* filter degree m; 0 = choose by eq. (thresh) (default 0) */
+  PFE_P_EPS_FRAC = 2,       /* margin eps as a fraction of eta - xi (default 0.25) */
+  PFE_P_RATE = 3,           /* convergence rate r of eq. (thresh) (default sqrt(0.1)) */
+  PFE_P_DAMPING = 4,        /* 0 none (default, best for subspace iteration in Sec. 4.1), 1 Jackson, 2 Lanczos sigma */
+  PFE_P_WIDTH = 5,          /* subspace width q; 0 = max(WIDTH_FACTOR * count estimate, 1.1 * window count
+                               estimate + 8, MIN_WIDTH), the window being [a - eps, b + eps] (default 0) */
+  PFE_P_WIDTH_FACTOR = 6,   /* default 1.5 */
+  PFE_P_TOL = 7,            /* residual tolerance ||H v - lambda v|| / lambda_max_est (default 1e-8) */
+  PFE_P_PRECISION = 8,      /* filter precision: 0 FP64 (default), 1 FP32 with FP64 refinement */
+  PFE_P_MAX_ITERS = 9,      /* subspace-iteration limit (default 60) */
+  PFE_P_SEED = 10,          /* seed of the random start block and estimator vectors (default 0) */
+  PFE_P_LAMBDA_MAX = 11,    /* spectrum upper bound; 0 = estimate by Lanczos (default 0) */
+  PFE_P_LAMBDA_MIN = 12,    /* spectrum lower bound (default 0: H is positive semidefinite) */
+  PFE_P_COUNT_M = 13,       /* number of estimator vectors M (default 30) */
+  PFE_P_COUNT_DEGREE = 14,  /* estimator degree (default 100) */
+  PFE_P_LANCZOS_STEPS = 15, /* Lanczos steps of the lambda_max estimate (default 30) */
+  PFE_P_COUNT_DAMPING = 16, /* damping of the estimator series (default 0: plain truncation) */
+  PFE_P_MIN_WIDTH = 17,     /* lower bound on the automatic width (default 16) */
+  PFE_P_REFINE_TOL = 18     /* FP32 mode: residual below which FP64 sweeps take over (default 1e-6) */
+};
+
+/* ---------------------------------------------------------------------------------------
+ * Setup (Sec. 3, Alg. 3; eq. (2) for the mass weighting)
+ * ------------------------------------------------------------------------------------- */
+
+/* Helper: assemble Delta of a spring network as BSR (eq. (1)): for every bond e = (i, j),
+ * i != j, with stiffness k[e] and unit vector rhat[3e..3e+2] (from i to j),
+ *   Delta_ij = Delta_ji = -k r r^T,  Delta_ii = -sum_{j != i} Delta_ij.
+ * Two-call pattern: with cap_nnzb < required (e.g. 0 and NULL outputs) it only stores the
+ * number of blocks in *nnzb and returns PFE_E_CAPACITY.  Host pointers, host computation.
+ * Duplicate bonds are summed.  Returns PFE_E_ARG for i == j or an index out of [0, N). */
+pfe_status pfe_springs_to_bsr(int32_t n_atoms, int64_t nbonds, const int32_t *bi, const int32_t *bj,
+                              const double *k, const double *rhat, int64_t cap_nnzb, int32_t *row_ptr,
+                              int32_t *col_idx, double *vals, int64_t *nnzb);
+
+/* Create a solver context for H = M^-1/2 Delta M^-1/2 (eq. (2)).
+ *   n_atoms N >= 1; nnzb = row_ptr[N]; masses[N] > 0, or NULL when vals already hold H.
+ *   flags: PFE_DEVICE_PTRS (inputs on the device), PFE_SKIP_SYM_CHECK.
+ *   cuda_stream: a cudaStream_t (NULL = default stream) used for all of the context's work.
+ * The structure is validated on the host (ranges, ascending columns, diagonal present,
+ * finite values, symmetry unless skipped).  Inputs are copied; H is formed on the device. */
+pfe_status pfe_create(pfe_ctx **out, int32_t n_atoms, int64_t nnzb, const int32_t *row_ptr,
+                      const int32_t *col_idx, const double *vals, const double *masses, uint32_t flags,
+                      void *cuda_stream);
+
+/* Release every device and host resource of the context (NULL is allowed). */
+void pfe_destroy(pfe_ctx *ctx);
+
+/* One-line description of the last failure on this context ("" if none). */
+const char *pfe_last_error(const pfe_ctx *ctx);
+
+pfe_status pfe_set_param(pfe_ctx *ctx, int key, double value);
+pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *value);
+
+/* The closed target interval [a, b] in lambda = omega^2 units, 0 <= a < b (eq. (intro.33)). */
+pfe_status pfe_set_interval(pfe_ctx *ctx, double a, double b);
+
+/* Alg. 3, set-up steps: bound lambda_max by a few Lanczos steps (unless PFE_P_LAMBDA_MAX is set),
+ * form the transform of eq. (transf.1), and estimate the number of eigenvalues in [a, b]
+ * with the stochastic trace estimator of Sec. 2.4 (eq. (eigval_count_estimator)).
+ * Either output pointer may be NULL.  Needs an interval for the count (else count = NaN). */
+pfe_status pfe_estimate(pfe_ctx *ctx, double *lambda_max, double *count_est);
+
+/* The filter the solver uses (Alg. 3; eqs. (fct_f), (thresh), App. A): degree in *m
+ * and the damped Chebyshev coefficients g_j gamma_j, j = 0..m, in coeffs[0..m] (host; may be
+ * NULL to query m only, cap = its length); c and d of eq. (transf.1).  Runs pfe_estimate's
+ * lambda_max step first if needed.  PFE_E_CAPACITY if cap < m + 1 (m still stored). */
+pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs, double *c, double *d);
+
+/* Alg. 3, solve step: compute all eigenpairs with lambda in [a, b] by filtered subspace iteration
+ * (Alg. 4 with Rayleigh-Ritz on H every iteration, CholQR2 orthonormalisation, locking).
+ * *n_found receives their number.  Results stay in the context.
+ * PFE_E_CAPACITY: the subspace was too narrow to certify completeness (raise PFE_P_WIDTH);
+ * PFE_E_NOCONV: the iteration limit was hit (partial results are kept). */
+pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found);
+
+/* Copy the results of the last pfe_solve: lambda[cap] ascending, vecs n x cap column-major
+ * (ld = n, unit 2-norm, mass-weighted coordinates q of eq. (3)), resid[cap] = ||H v - lambda v||
+ * (absolute).  Any output may be NULL.  flags: PFE_DEVICE_PTRS for device output buffers.
+ * PFE_E_CAPACITY if cap < n_found (nothing copied).  Also reports iteration statistics via
+ * pfe_get_param-style keys in pfe_get_stats. */
+pfe_status pfe_get_eigenpairs(pfe_ctx *ctx, int32_t cap, double *lambda, double *vecs, double *resid,
+                              uint32_t flags);
+
+/* Statistics of the last solve: iterations, single-vector products with H (the paper's
+ * MatVec count, Sec. 4.1), subspace width, degree, filter seconds, total seconds. */
+typedef struct {
+  int32_t iterations;
+  int32_t width;
+  int32_t degree;
+  int32_t n_found;
+  int64_t matvecs;
+  double lambda_max;
+  double count_estimate;
+  double seconds_total;
+  double seconds_filter;
+  double seconds_orth;
+  double seconds_rr;
+  double max_residual;
+  int32_t fp64_sweeps; /* FP32 mode: iterations run with the FP64 filter */
+  int32_t status;
+  double window_estimate; /* estimated eigenvalue count of the margin window (automatic width only) */
+} pfe_stats;
+pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
+
+/* ---------------------------------------------------------------------------------------
+ * The filter (Alg. 2, the operator of Sec. 3) and its adjoint
+ * ------------------------------------------------------------------------------------- */
+
+/* Y = p_m(Ht) X with Ht = (H - cI)/d (eq. (transf.1)) and p_m = sum_{j<=m} coeffs[j] T_j
+ * (Alg. 2; coeffs on the host, m + 1 of them, or NULL for the solver's own filter, in
+ * which case m is ignored).  X and Y are DEVICE pointers, column-major n x k with leading
+ * dimensions ldx, ldy >= n, element type dtype (PFE_F64 or PFE_F32, the same for X and Y;
+ * PFE_F32 runs the recurrence in FP32 arithmetic).  Y must not overlap X.  k may be 0 (no-op).  c, d come from the context
+ * (PFE_P_LAMBDA_MAX / _MIN or the Lanczos estimate).  stream: cudaStream_t or NULL for the
+ * context's stream.  Work buffers are allocated by the context and kept for reuse. */
+pfe_status pfe_filter_apply(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const void *X,
+                            int64_t ldx, void *Y, int64_t ldy, int dtype, void *stream);
+
+/* Adjoint of Y = p_m(Ht) X for L = <Ybar, Y> with c, d held fixed (FP64 only):
+ *   Xbar = p_m(Ht)^T Ybar = p_m(Ht) Ybar,
+ *   vals_bar[9 nnzb] = dL/dH for each stored entry of H (same layout as vals).
+ * The recurrence is recomputed from about sqrt(m) stored checkpoints of (t_j, t_{j-1}).
+ * All arrays are DEVICE pointers; X, Ybar, Xbar column-major n x k.  vals_bar is overwritten. */
+pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const double *X,
+                              int64_t ldx, const double *Ybar, int64_t ldyb, double *Xbar, int64_t ldxb,
+                              double *vals_bar, void *stream);
+
+/* Chain rule from vals_bar = dL/dH (per stored entry, as returned by pfe_filter_adjoint) to the
+ * spring constants and masses of the network that pfe_springs_to_bsr assembled (eq. (2)):
+ *   k_bar[e] = dL/dk_e,  m_bar[i] = dL/dm_i.
+ * DEVICE pointers: bi, bj (int32), rhat (3 per bond), vals_bar, k_bar (nbonds), m_bar (N).
+ * Needs a context created with masses. */
+pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, const int32_t *bj,
+                             const double *rhat, const double *vals_bar, double *k_bar, double *m_bar,
+                             void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched solves of independent samples (the realisations H_1 .. H_8 of Sec. 4.2)
+ * ------------------------------------------------------------------------------------- */
+
+/* Solve every context's interval problem; n_found[s] per sample.  Each context must have its
+ * interval set.  Returns the first failing status (the others still run). */
+pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFE_H */

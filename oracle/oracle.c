@@ -178,7 +178,7 @@ void or_spmm(const or_csr *A, int32_t k, const double *X, int64_t ldx, double *Y
   }
 }
 
-/* r_i = || A v_i - lam_i v_i ||_2 for k pairs (the residual of Alg. 3, line 7). */
+/* r_i = || A v_i - lam_i v_i ||_2 for k pairs (the residual reported by Alg. 3). */
 void or_residuals(const or_csr *A, int32_t k, const double *lam, const double *V, int64_t ldv, double *res) {
   double *w = (double *)malloc(sizeof(double) * (size_t)A->n);
   for (int32_t c = 0; c < k; ++c) {
@@ -584,7 +584,7 @@ int64_t or_count_below(int32_t n, const double *diag, const double *off, double 
 }
 
 /* ======================================================================================
- * Extremal eigenvalue estimate (Alg. 3, line 3): Lanczos with full reorthogonalisation.
+ * Extremal eigenvalue estimate (Alg. 3, a few Lanczos steps): Lanczos with full reorthogonalisation.
  * lmax_est = max(1.01 theta_max, theta_max + |beta_s s_s|), s the Ritz vector of theta_max.
  * The start vector is column 0 of random stream 1.
  * ==================================================================================== */

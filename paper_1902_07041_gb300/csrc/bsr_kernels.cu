@@ -1,0 +1,342 @@
+// BSR kernels of the filter: the fused Chebyshev step of Alg. 2 over 3x3 blocks, the mass
+// weighting of eq. (2), the scaled filter operator of eq. (transf.1), and the adjoint's
+// outer products and chain rule.
+//
+// Multivector layout: row-major n x k with row stride ld (the k columns of one dof row are
+// contiguous).  The three dof rows of atom j are then 3k contiguous values, so gathering a
+// neighbour's rows is one coalesced sweep per row.  One warp owns (atom i, a chunk of
+// 32 * CPL columns); each lane owns CPL adjacent columns and keeps 3 x CPL accumulators.
+// Block values and column indices are warp-uniform loads (served as L1 broadcasts); every
+// 3x3 block is read once per column chunk.
+#include "pfe_internal.h"
+
+namespace pfe {
+namespace {
+
+// ---- vector loads/stores of CPL adjacent elements ------------------------------------
+__device__ __forceinline__ void ldg_n(const double *p, double (&v)[1]) { v[0] = __ldg(p); }
+__device__ __forceinline__ void ldg_n(const double *p, double (&v)[2]) {
+  double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+}
+__device__ __forceinline__ void ldg_n(const float *p, float (&v)[1]) { v[0] = __ldg(p); }
+__device__ __forceinline__ void ldg_n(const float *p, float (&v)[2]) {
+  float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+}
+__device__ __forceinline__ void ldg_n(const float *p, float (&v)[4]) {
+  float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void ld_n(const double *p, double (&v)[1]) { v[0] = *p; }
+__device__ __forceinline__ void ld_n(const double *p, double (&v)[2]) {
+  double2 t = *reinterpret_cast<const double2 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+__device__ __forceinline__ void ld_n(const float *p, float (&v)[1]) { v[0] = *p; }
+__device__ __forceinline__ void ld_n(const float *p, float (&v)[2]) {
+  float2 t = *reinterpret_cast<const float2 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+}
+__device__ __forceinline__ void ld_n(const float *p, float (&v)[4]) {
+  float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
+__device__ __forceinline__ void st_n(double *p, const double (&v)[1]) { *p = v[0]; }
+__device__ __forceinline__ void st_n(double *p, const double (&v)[2]) {
+  *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void st_n(float *p, const float (&v)[1]) { *p = v[0]; }
+__device__ __forceinline__ void st_n(float *p, const float (&v)[2]) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+__device__ __forceinline__ void st_n(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// ---- the fused step -------------------------------------------------------------------
+// SPMM : Z = alpha A X
+// FIRST: Z = alpha A X;          Y = g0 X + g1 Z            (t_1 and p_1(H)x of Alg. 2)
+// STEP : Z = alpha A X + beta W; Y += g1 Z                  (t_{j+1} = 2 Ht t_j - t_{j-1})
+// ADJ  : Z = alpha A X + beta W + g0 Y   (Y read-only)      (reverse sweep of the adjoint)
+// With A = (2/d)(H - cI) the step needs alpha = 1, beta = -1; the first step alpha = 1/2.
+template <typename T, int CPL, int MODE>
+__global__ void __launch_bounds__(256) k_bsr_step(int32_t n_atoms, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ ci, const T *__restrict__ vals,
+                                                  int32_t k, int64_t ld, int32_t nchunk, const T *__restrict__ X,
+                                                  const T *W, T *Z, T *Y, T alpha, T beta, T g0, T g1) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t atom = gw / nchunk;
+  if (atom >= n_atoms) return;
+  const int chunk = (int)(gw - atom * nchunk);
+  const int c0 = (chunk * 32 + lane) * CPL;
+  const bool on = c0 < k;
+  T acc[3][CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) acc[0][c] = acc[1][c] = acc[2][c] = T(0);
+  const int p0 = __ldg(rp + atom), p1 = __ldg(rp + atom + 1);
+  for (int p = p0; p < p1; ++p) {
+    const int64_t j = __ldg(ci + p);
+    const T *v = vals + 9 * (int64_t)p;
+    T a[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) a[t] = __ldg(v + t);
+    if (on) {
+      const T *xr = X + 3 * j * ld + c0;
+      T x0[CPL], x1[CPL], x2[CPL];
+      ldg_n(xr, x0);
+      ldg_n(xr + ld, x1);
+      ldg_n(xr + 2 * ld, x2);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        acc[0][c] = fma(a[0], x0[c], fma(a[1], x1[c], fma(a[2], x2[c], acc[0][c])));
+        acc[1][c] = fma(a[3], x0[c], fma(a[4], x1[c], fma(a[5], x2[c], acc[1][c])));
+        acc[2][c] = fma(a[6], x0[c], fma(a[7], x1[c], fma(a[8], x2[c], acc[2][c])));
+      }
+    }
+  }
+  if (!on) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int64_t off = (3 * atom + r) * ld + c0;
+    T z[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) z[c] = alpha * acc[r][c];
+    if (MODE == MODE_STEP || MODE == MODE_ADJ) {
+      T w[CPL];
+      ld_n(W + off, w);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) z[c] = fma(beta, w[c], z[c]);
+    }
+    if (MODE == MODE_ADJ) {
+      T y[CPL];
+      ld_n(Y + off, y);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) z[c] = fma(g0, y[c], z[c]);
+    }
+    st_n(Z + off, z);
+    if (MODE == MODE_FIRST) {
+      T x[CPL], y[CPL];
+      ldg_n(X + off, x);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], g0 * x[c]);
+      st_n(Y + off, y);
+    } else if (MODE == MODE_STEP && Y != nullptr) {
+      T y[CPL];
+      ld_n(Y + off, y);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      st_n(Y + off, y);
+    }
+  }
+}
+
+template <typename T, int CPL>
+void dispatch_mode(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
+                   T beta, T g0, T g1, cudaStream_t s) {
+  const int32_t nchunk = (k + 32 * CPL - 1) / (32 * CPL);
+  const int64_t threads = (int64_t)A.n_atoms * nchunk * 32;
+  const int64_t blocks = (threads + 255) / 256;
+  if (mode == MODE_SPMM)
+    k_bsr_step<T, CPL, MODE_SPMM><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+                                                                  Z, Y, alpha, beta, g0, g1);
+  else if (mode == MODE_FIRST)
+    k_bsr_step<T, CPL, MODE_FIRST><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X,
+                                                                   W, Z, Y, alpha, beta, g0, g1);
+  else if (mode == MODE_ADJ)
+    k_bsr_step<T, CPL, MODE_ADJ><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+                                                                 Z, Y, alpha, beta, g0, g1);
+  else
+    k_bsr_step<T, CPL, MODE_STEP><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+                                                                  Z, Y, alpha, beta, g0, g1);
+}
+
+bool aligned(const void *p, size_t a) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
+
+template <>
+void launch_bsr_step<double>(const Bsr<double> &A, int mode, int32_t k, int64_t ld, const double *X, const double *W,
+                             double *Z, double *Y, double alpha, double beta, double g0, double g1, cudaStream_t s) {
+  if (k <= 0 || A.n_atoms <= 0) return;
+  const bool v2 = k > 32 && ld % 2 == 0 && aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
+  if (v2)
+    dispatch_mode<double, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  else
+    dispatch_mode<double, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+}
+
+template <>
+void launch_bsr_step<float>(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W,
+                            float *Z, float *Y, float alpha, float beta, float g0, float g1, cudaStream_t s) {
+  if (k <= 0 || A.n_atoms <= 0) return;
+  const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
+  const bool al8 = aligned(X, 8) && aligned(W, 8) && aligned(Z, 8) && aligned(Y, 8);
+  if (k > 64 && ld % 4 == 0 && al16)
+    dispatch_mode<float, 4>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  else if (k > 32 && ld % 2 == 0 && al8)
+    dispatch_mode<float, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  else
+    dispatch_mode<float, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+}
+
+// ---- a0: mass weighting, one warp per atom row ----------------------------------------
+namespace {
+__global__ void k_mass_weight(int32_t n_atoms, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const double *__restrict__ delta, const double *__restrict__ mass, double *H) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_atoms) return;
+  const double mi = mass[i];
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+    const double s = sqrt(mi * mass[ci[p]]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) H[9 * (int64_t)p + t] = delta[9 * (int64_t)p + t] / s;
+  }
+}
+
+__global__ void k_filter_matrix(int32_t n_atoms, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                const double *__restrict__ H, double alpha, double shift, double *out64,
+                                float *out32) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_atoms) return;
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+    const bool diag = ci[p] == i;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const double h = H[9 * (int64_t)p + t] - ((diag && (t == 0 || t == 4 || t == 8)) ? shift : 0.0);
+      const double v = alpha * h;
+      if (out64) out64[9 * (int64_t)p + t] = v;
+      if (out32) out32[9 * (int64_t)p + t] = (float)v;
+    }
+  }
+}
+
+__device__ int find_block(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t row, int32_t col) {
+  int lo = rp[row], hi = rp[row + 1] - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = ci[mid];
+    if (c == col) return mid;
+    if (c < col) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+__device__ double rbr(const double *__restrict__ blk, const double r0, const double r1, const double r2) {
+  // r^T B r for a row-major 3x3 block B
+  return r0 * (blk[0] * r0 + blk[1] * r1 + blk[2] * r2) + r1 * (blk[3] * r0 + blk[4] * r1 + blk[5] * r2) +
+         r2 * (blk[6] * r0 + blk[7] * r1 + blk[8] * r2);
+}
+
+__global__ void k_chain_k(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ mass,
+                          int64_t nbonds, const int32_t *__restrict__ bi, const int32_t *__restrict__ bj,
+                          const double *__restrict__ rhat, const double *__restrict__ hbar, double *kbar) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nbonds) return;
+  const int32_t i = bi[e], j = bj[e];
+  const double r0 = rhat[3 * e], r1 = rhat[3 * e + 1], r2 = rhat[3 * e + 2];
+  const int pij = find_block(rp, ci, i, j), pji = find_block(rp, ci, j, i);
+  const int pii = find_block(rp, ci, i, i), pjj = find_block(rp, ci, j, j);
+  if (pij < 0 || pji < 0 || pii < 0 || pjj < 0) {
+    kbar[e] = __longlong_as_double(0x7ff8000000000000ULL);  // NaN: bond not in the pattern
+    return;
+  }
+  const double off = rbr(hbar + 9 * (int64_t)pij, r0, r1, r2) + rbr(hbar + 9 * (int64_t)pji, r0, r1, r2);
+  kbar[e] = -off / sqrt(mass[i] * mass[j]) + rbr(hbar + 9 * (int64_t)pii, r0, r1, r2) / mass[i] +
+            rbr(hbar + 9 * (int64_t)pjj, r0, r1, r2) / mass[j];
+}
+
+__global__ void k_chain_m(int32_t n_atoms, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ H, const double *__restrict__ mass,
+                          const double *__restrict__ hbar, double *mbar) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_atoms) return;
+  double off = 0.0, dia = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int32_t j = ci[p];
+    double s = 0.0;
+    for (int t = 0; t < 9; ++t) s += hbar[9 * (int64_t)p + t] * H[9 * (int64_t)p + t];
+    if (j == i) {
+      dia += s;
+      continue;
+    }
+    off += s;
+    const int q = find_block(rp, ci, j, (int32_t)i);
+    if (q >= 0)
+      for (int t = 0; t < 9; ++t) off += hbar[9 * (int64_t)q + t] * H[9 * (int64_t)q + t];
+  }
+  mbar[i] = -off / (2.0 * mass[i]) - dia / mass[i];
+}
+
+// hbar[9p + 3r + s] += alpha * sum_c A[3i + r, c] * Tm[3j + s, c]; one warp per atom row i
+template <typename T>
+__global__ void k_outer_accum(int32_t n_atoms, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              int32_t k, int64_t ld, const T *__restrict__ A, const T *__restrict__ Tm, double alpha,
+                              double *hbar) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_atoms) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int64_t j = ci[p];
+    double s[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) s[t] = 0.0;
+    for (int c = lane; c < k; c += 32) {
+      const double a0 = A[(3 * i) * ld + c], a1 = A[(3 * i + 1) * ld + c], a2 = A[(3 * i + 2) * ld + c];
+      const double t0 = Tm[(3 * j) * ld + c], t1 = Tm[(3 * j + 1) * ld + c], t2 = Tm[(3 * j + 2) * ld + c];
+      s[0] += a0 * t0; s[1] += a0 * t1; s[2] += a0 * t2;
+      s[3] += a1 * t0; s[4] += a1 * t1; s[5] += a1 * t2;
+      s[6] += a2 * t0; s[7] += a2 * t1; s[8] += a2 * t2;
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+      for (int o = 16; o > 0; o >>= 1) s[t] += __shfl_xor_sync(0xffffffffu, s[t], o);
+    if (lane == 0)
+      for (int t = 0; t < 9; ++t) hbar[9 * (int64_t)p + t] += alpha * s[t];
+  }
+}
+}  // namespace
+
+void launch_mass_weight(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *delta, const double *mass,
+                        double *H, cudaStream_t s) {
+  const int64_t blocks = ((int64_t)n_atoms * 32 + 255) / 256;
+  k_mass_weight<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, delta, mass, H);
+}
+
+void launch_filter_matrix(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha,
+                          double shift, double *out64, float *out32, cudaStream_t s) {
+  const int64_t blocks = ((int64_t)n_atoms * 32 + 255) / 256;
+  k_filter_matrix<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, H, alpha, shift, out64, out32);
+}
+
+void launch_chain_springs(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, const double *mass,
+                          int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *rhat, const double *hbar,
+                          double *kbar, double *mbar, cudaStream_t s) {
+  if (nbonds > 0) k_chain_k<<<(unsigned)((nbonds + 255) / 256), 256, 0, s>>>(rp, ci, mass, nbonds, bi, bj, rhat, hbar, kbar);
+  if (n_atoms > 0) k_chain_m<<<(unsigned)((n_atoms + 255) / 256), 256, 0, s>>>(n_atoms, rp, ci, H, mass, hbar, mbar);
+}
+
+template <typename T>
+void launch_outer_accum(const Bsr<T> &pattern, int32_t k, int64_t ld, const T *A, const T *Tm, double alpha,
+                        double *hbar, cudaStream_t s) {
+  const int64_t blocks = ((int64_t)pattern.n_atoms * 32 + 255) / 256;
+  k_outer_accum<T><<<(unsigned)blocks, 256, 0, s>>>(pattern.n_atoms, pattern.rp, pattern.ci, k, ld, A, Tm, alpha, hbar);
+}
+template void launch_outer_accum<double>(const Bsr<double> &, int32_t, int64_t, const double *, const double *, double,
+                                         double *, cudaStream_t);
+
+}  // namespace pfe

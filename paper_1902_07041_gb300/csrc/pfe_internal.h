@@ -1,0 +1,198 @@
+// Internal declarations of the GB300 polynomial-filtered eigensolver library (libpfe).
+// Host control (solver.cu), kernels (bsr_kernels.cu, vec_kernels.cu) and host math
+// (filter_host.cu) meet here.  Nothing in this directory is shared with the CPU oracle.
+#pragma once
+
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pfe.h"
+
+namespace pfe {
+
+// --------------------------------------------------------------------------------------
+// Device buffers
+// --------------------------------------------------------------------------------------
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  template <typename T>
+  T *as() const { return static_cast<T *>(p); }
+};
+cudaError_t dbuf_reserve(DBuf &b, size_t bytes);  // grow-only, contents not preserved
+void dbuf_free(DBuf &b);
+
+// --------------------------------------------------------------------------------------
+// BSR matrix on the device (3x3 blocks, row-major inside a block)
+// --------------------------------------------------------------------------------------
+template <typename T>
+struct Bsr {
+  int32_t n_atoms = 0;
+  const int32_t *rp = nullptr;
+  const int32_t *ci = nullptr;
+  const T *vals = nullptr;
+};
+
+// Step modes of the fused BSR kernel (row-major n x k multivectors with row stride ld):
+//   SPMM : Z = alpha A X
+//   FIRST: Z = alpha A X;              Y = g0 X + g1 Z
+//   STEP : Z = alpha A X + beta W;     Y = Y + g1 Z        (W may alias Z; Y may be null)
+//   ADJ  : Z = alpha A X + beta W + g0 Y                   (Y read-only; W may alias Z)
+enum StepMode { MODE_SPMM = 0, MODE_FIRST = 1, MODE_STEP = 2, MODE_ADJ = 3 };
+
+template <typename T>
+void launch_bsr_step(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
+                     T beta, T g0, T g1, cudaStream_t s);
+
+// a0: H = Delta / sqrt(m_i m_j) per block; also the row index of each block
+void launch_mass_weight(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *delta, const double *mass,
+                        double *H, cudaStream_t s);
+// Filter operator Hs = alpha (H - shift I), in FP64 and (optionally) FP32
+void launch_filter_matrix(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha,
+                          double shift, double *out64, float *out32, cudaStream_t s);
+// Chain rule dL/dH (per stored entry) -> dL/dk, dL/dm
+void launch_chain_springs(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, const double *mass,
+                          int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *rhat, const double *hbar,
+                          double *kbar, double *mbar, cudaStream_t s);
+// Adjoint outer-product accumulation: hbar[p] += alpha * sum_c A[i, c] T[j, c] over block p = (i, j)
+template <typename T>
+void launch_outer_accum(const Bsr<T> &pattern, int32_t k, int64_t ld, const T *A, const T *Tm, double alpha,
+                        double *hbar, cudaStream_t s);
+
+// --------------------------------------------------------------------------------------
+// Dense helpers (row-major n x k blocks with row stride ld unless stated)
+// --------------------------------------------------------------------------------------
+// Philox4x32-10 normals: element (row i, column col0 + c) of stream `stream`
+template <typename T>
+void launch_fill_normal(uint64_t seed, uint32_t stream_id, int64_t n, int32_t k, int32_t col0, T *X, int64_t ld,
+                        cudaStream_t s);
+// out[c] = sum_i X[i,c] * Y[i,c] (deterministic two-pass); work >= colreduce_work(n, k) doubles
+size_t colreduce_work(int64_t n, int32_t k);
+template <typename T>
+void launch_col_dots(int64_t n, int32_t k, const T *X, int64_t ldx, const T *Y, int64_t ldy, double *out, double *work,
+                     cudaStream_t s);
+// out[c] = || W[:,c] - theta[c] X[:,c] ||^2
+void launch_col_resid2(int64_t n, int32_t k, const double *W, const double *X, int64_t ld, const double *theta,
+                       double *out, double *work, cudaStream_t s);
+template <typename T>
+void launch_scale_cols(int64_t n, int32_t k, T *X, int64_t ld, const double *scale, cudaStream_t s);
+template <typename T>
+void launch_axpby(int64_t n, int32_t k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, cudaStream_t s);
+template <typename Tin, typename Tout>
+void launch_convert(int64_t n, int32_t k, const Tin *X, int64_t ldx, Tout *Y, int64_t ldy, cudaStream_t s);
+// dst[:, t] = src[:, idx[t]] (idx on the device)
+void launch_gather_cols(int64_t n, int32_t kdst, const double *src, int64_t lds, double *dst, int64_t ldd,
+                        const int32_t *idx, cudaStream_t s);
+// column-major (n x k, ldc) <-> row-major (n x k, ldr)
+template <typename T>
+void launch_colmajor_to_rowmajor(int64_t n, int32_t k, const T *C, int64_t ldc, T *R, int64_t ldr, cudaStream_t s);
+template <typename T>
+void launch_rowmajor_to_colmajor(int64_t n, int32_t k, const T *R, int64_t ldr, T *C, int64_t ldc, cudaStream_t s);
+template <typename T>
+void launch_zero(T *p, int64_t count, cudaStream_t s);
+
+// --------------------------------------------------------------------------------------
+// Host math of the filter (App. A, Sec. 2.3, eq. (thresh)); independent of the oracle
+// --------------------------------------------------------------------------------------
+// gamma_0..gamma_m of the piecewise quadratic p of eq. (fct_f)
+void pq_coefficients(double xi, double eta, double eps, int32_t m, std::vector<double> &gamma);
+// gamma_0..gamma_m of the characteristic function of [xi, eta]
+void chi_coefficients(double xi, double eta, int32_t m, std::vector<double> &gamma);
+// damping factors g_0..g_m (0 none, 1 Jackson, 2 Lanczos sigma)
+void damping_factors(int kind, int32_t m, std::vector<double> &g);
+// value of sum c_j T_j(x)
+double chebyshev_value(const std::vector<double> &c, int32_t m, double x);
+// smallest degree satisfying eq. (thresh), or -1
+int32_t choose_degree(double xi, double eta, double eps, double r, int kind, int32_t kmax);
+// largest eigenvalue of a symmetric tridiagonal matrix and the last entry of its unit eigenvector
+void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &beta, double *theta, double *last);
+
+}  // namespace pfe
+
+// --------------------------------------------------------------------------------------
+// The context
+// --------------------------------------------------------------------------------------
+struct pfe_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  int32_t N = 0;
+  int64_t n = 0;
+  int64_t nnzb = 0;
+  bool has_mass = false;
+  pfe::DBuf rp, ci, H, mass, Hs64, Hs32;
+  double hs_c = 0, hs_d = 0;  // transform the filter matrices were built for
+  bool hs_valid = false, hs32_valid = false;
+
+  // parameters
+  int32_t p_degree = 0;
+  double p_eps_frac = 0.25;
+  double p_rate = 0.31622776601683794;
+  int p_damping = 0;
+  int32_t p_width = 0;
+  double p_width_factor = 1.5;
+  double p_tol = 1e-8;
+  int p_precision = 0;
+  int32_t p_max_iters = 60;
+  uint64_t p_seed = 0;
+  double p_lambda_max = 0, p_lambda_min = 0;
+  int32_t p_count_m = 30, p_count_degree = 100, p_lanczos_steps = 30;
+  int p_count_damping = 0;
+  int32_t p_min_width = 16;
+  double p_refine_tol = 1e-6;
+
+  // state
+  bool has_interval = false;
+  double a = 0, b = 0;
+  bool has_lmax = false;
+  double lmax = 0, theta_max = 0, lanczos_resid = 0;
+  bool has_count = false;
+  double count_est = 0;
+  bool has_filter = false;
+  int32_t m = 0;
+  std::vector<double> coef;
+  double tc = 0, td = 0, xi = 0, eta = 0, eps = 0;
+
+  // results
+  bool has_result = false;
+  int32_t n_found = 0;
+  pfe::DBuf L;          // locked vectors, row-major n x ldq
+  int64_t ldq = 0;
+  std::vector<int32_t> result_cols;  // columns of L in ascending eigenvalue order
+  std::vector<double> result_lam, result_res;
+  pfe_stats stats{};
+
+  // workspaces
+  pfe::DBuf w_X, w_Y, w_W, w_T0, w_T1, w_T2, w_small, w_small2, w_red, w_idx, w_cs_work, w_info, w_f32a, w_f32b,
+      w_f32c, w_f32d, w_ckpt, w_rr;
+  std::string err;
+};
+
+// status helpers used across the host sources
+pfe_status pfe_fail(pfe_ctx *ctx, pfe_status st, const std::string &msg);
+#define PFE_CUDA_TRY(ctx, call)                                                                          \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) return pfe_fail((ctx), PFE_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define PFE_BLAS_TRY(ctx, call)                                                                      \
+  do {                                                                                               \
+    cublasStatus_t e_ = (call);                                                                      \
+    if (e_ != CUBLAS_STATUS_SUCCESS) return pfe_fail((ctx), PFE_E_CUDA, std::string(#call) + " failed (cublas " + std::to_string((int)e_) + ")"); \
+  } while (0)
+#define PFE_SOLVER_TRY(ctx, call)                                                                      \
+  do {                                                                                                 \
+    cusolverStatus_t e_ = (call);                                                                      \
+    if (e_ != CUSOLVER_STATUS_SUCCESS) return pfe_fail((ctx), PFE_E_CUDA, std::string(#call) + " failed (cusolver " + std::to_string((int)e_) + ")"); \
+  } while (0)
+#define PFE_TRY(call)                    \
+  do {                                   \
+    pfe_status st_ = (call);             \
+    if (st_ != PFE_OK) return st_;       \
+  } while (0)

@@ -1,0 +1,1101 @@
+// The C ABI of libpfe and the host control of the filtered subspace iteration.
+//
+// Path of pfe_solve (Sec. 2.6, Alg. 3, Alg. 4 with Rayleigh-Ritz each iteration and locking):
+//   Lanczos bound on lambda_max -> transform (eq. (transf.1)) -> coefficients and degree
+//   (App. A, eq. (thresh)) -> eigenvalue-count estimate (Sec. 2.4) -> random start block ->
+//   loop { Y = p_m(Ht) X (fused BSR kernel, m launches) ; Y -= L L^T Y ; CholQR2(Y) ;
+//          W = H X ; Rayleigh-Ritz ; residuals ; lock } .
+// The only device-to-host traffic per iteration is the q Ritz values and residual norms.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "pfe_internal.h"
+
+using namespace pfe;
+
+pfe_status pfe_fail(pfe_ctx *ctx, pfe_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+T *reserve(pfe_ctx *ctx, DBuf &b, size_t count, pfe_status *st) {
+  cudaError_t e = dbuf_reserve(b, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *st = pfe_fail(ctx, PFE_E_NOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                         " bytes failed: " + cudaGetErrorString(e));
+    return nullptr;
+  }
+  *st = PFE_OK;
+  return b.as<T>();
+}
+
+#define RESERVE(T, ptr, buf, count)                 \
+  T *ptr = nullptr;                                 \
+  {                                                 \
+    pfe_status st__;                                \
+    ptr = reserve<T>(ctx, (buf), (count), &st__);   \
+    if (st__ != PFE_OK) return st__;                \
+  }
+
+Bsr<double> bsr_H(const pfe_ctx *ctx) { return Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>()}; }
+Bsr<double> bsr_Hs64(const pfe_ctx *ctx) { return Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs64.as<double>()}; }
+Bsr<float> bsr_Hs32(const pfe_ctx *ctx) { return Bsr<float>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs32.as<float>()}; }
+
+pfe_status check_launch(pfe_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return PFE_OK;
+}
+
+// ---------------------------------------------------------------- the filter driver (Alg. 2)
+// Y = sum_j coef[j] T_j(Ht) X with A = (2/d)(H - cI) = 2 Ht:
+//   t_1 = A t_0 / 2, t_{j+1} = A t_j - t_{j-1}; y accumulated in the same launch.
+// X is read-only; b0, b1 are two scratch multivectors of the same shape.
+template <typename T>
+pfe_status run_filter(pfe_ctx *ctx, const Bsr<T> &A, const double *coef, int32_t m, int32_t k, int64_t ld, const T *X,
+                      T *Y, T *b0, T *b1, cudaStream_t s) {
+  if (k <= 0) return PFE_OK;
+  if (m == 0) {
+    launch_axpby<T>(ctx->n, k, (T)coef[0], X, ld, T(0), Y, ld, s);
+    return check_launch(ctx, "filter (degree 0)");
+  }
+  launch_bsr_step<T>(A, MODE_FIRST, k, ld, X, nullptr, b0, Y, T(0.5), T(0), (T)coef[0], (T)coef[1], s);
+  const T *tprev = X;
+  T *tcur = b0;
+  for (int32_t j = 1; j < m; ++j) {
+    T *out = (tprev == X) ? b1 : const_cast<T *>(tprev);
+    launch_bsr_step<T>(A, MODE_STEP, k, ld, tcur, tprev, out, Y, T(1), T(-1), T(0), (T)coef[j + 1], s);
+    tprev = tcur;
+    tcur = out;
+  }
+  return check_launch(ctx, "filter step");
+}
+
+// ---------------------------------------------------------------- set-up helpers
+pfe_status ensure_lmax(pfe_ctx *ctx);
+
+pfe_status lanczos_bound(pfe_ctx *ctx) {
+  const int64_t n = ctx->n;
+  const int32_t steps = (int32_t)std::min<int64_t>(std::max(ctx->p_lanczos_steps, 1), n);
+  cudaStream_t s = ctx->stream;
+  RESERVE(double, V, ctx->w_T0, (size_t)n * (steps + 1));
+  RESERVE(double, w, ctx->w_T1, (size_t)n);
+  RESERVE(double, h, ctx->w_small, (size_t)steps + 8);
+  RESERVE(double, red, ctx->w_red, colreduce_work(n, 1) + 8);
+  double *scal = h + steps + 1;  // one device scalar
+  Bsr<double> A = bsr_H(ctx);
+  launch_fill_normal<double>(ctx->p_seed, 1u, n, 1, 0, V, 1, s);
+  launch_col_dots<double>(n, 1, V, 1, V, 1, scal, red, s);
+  double nv = 0.0;
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&nv, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (!(nv > 0.0) || !std::isfinite(nv)) return pfe_fail(ctx, PFE_E_BREAKDOWN, "Lanczos start vector is zero");
+  {
+    std::vector<double> sc(1, 1.0 / std::sqrt(nv));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(scal, sc.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_scale_cols<double>(n, 1, V, 1, scal, s);
+  }
+  std::vector<double> al, be;
+  const double one = 1.0, zero = 0.0, mone = -1.0;
+  for (int32_t j = 0; j < steps; ++j) {
+    double *vj = V + (int64_t)j * n;
+    launch_bsr_step<double>(A, MODE_SPMM, 1, 1, vj, nullptr, w, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+    // full reorthogonalisation against v_0..v_j (two classical Gram-Schmidt passes); the first
+    // pass also yields alpha_j = v_j^T w and removes alpha_j v_j + beta_{j-1} v_{j-1}
+    double aj = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      PFE_BLAS_TRY(ctx, cublasDgemv(ctx->blas, CUBLAS_OP_T, (int)n, j + 1, &one, V, (int)n, w, 1, &zero, h, 1));
+      if (pass == 0) {
+        PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&aj, h + j, sizeof(double), cudaMemcpyDeviceToHost, s));
+      }
+      PFE_BLAS_TRY(ctx, cublasDgemv(ctx->blas, CUBLAS_OP_N, (int)n, j + 1, &mone, V, (int)n, h, 1, &one, w, 1));
+    }
+    launch_col_dots<double>(n, 1, w, 1, w, 1, scal, red, s);
+    double bb = 0.0;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&bb, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    al.push_back(aj);
+    const double bj = std::sqrt(std::max(bb, 0.0));
+    be.push_back(bj);
+    if (!(bj > 1e-300) || j + 1 == steps) break;
+    std::vector<double> sc(1, 1.0 / bj);
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(scal, sc.data(), sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_axpby<double>(n, 1, 1.0, w, 1, 0.0, V + (int64_t)(j + 1) * n, 1, s);
+    launch_scale_cols<double>(n, 1, V + (int64_t)(j + 1) * n, 1, scal, s);
+    PFE_TRY(check_launch(ctx, "Lanczos"));
+  }
+  double th = 0.0, last = 0.0;
+  std::vector<double> offd(be.begin(), be.end() - 1);
+  tridiag_top(al, offd, &th, &last);
+  const double rb = std::fabs(be.back() * last);
+  ctx->theta_max = th;
+  ctx->lanczos_resid = rb;
+  ctx->lmax = std::max(1.01 * th, th + rb);
+  return PFE_OK;
+}
+
+void set_transform(pfe_ctx *ctx) {
+  ctx->tc = 0.5 * (ctx->lmax + ctx->p_lambda_min);
+  ctx->td = 0.5 * (ctx->lmax - ctx->p_lambda_min);
+}
+
+pfe_status ensure_lmax(pfe_ctx *ctx) {
+  if (ctx->has_lmax) return PFE_OK;
+  if (ctx->p_lambda_max > 0) {
+    ctx->lmax = ctx->p_lambda_max;
+    ctx->theta_max = ctx->lanczos_resid = 0;
+  } else {
+    PFE_TRY(lanczos_bound(ctx));
+  }
+  if (!(ctx->lmax > ctx->p_lambda_min)) return pfe_fail(ctx, PFE_E_ARG, "lambda_max must exceed lambda_min");
+  set_transform(ctx);
+  ctx->has_lmax = true;
+  ctx->hs_valid = ctx->hs32_valid = false;
+  return PFE_OK;
+}
+
+pfe_status ensure_hs(pfe_ctx *ctx, bool need32) {
+  PFE_TRY(ensure_lmax(ctx));
+  const bool same = ctx->hs_c == ctx->tc && ctx->hs_d == ctx->td;
+  if (same && ctx->hs_valid && (!need32 || ctx->hs32_valid)) return PFE_OK;
+  RESERVE(double, h64, ctx->Hs64, (size_t)9 * ctx->nnzb);
+  float *h32 = nullptr;
+  if (need32) {
+    RESERVE(float, p32, ctx->Hs32, (size_t)9 * ctx->nnzb);
+    h32 = p32;
+  }
+  launch_filter_matrix(ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>(), 2.0 / ctx->td, ctx->tc,
+                       h64, h32, ctx->stream);
+  PFE_TRY(check_launch(ctx, "filter matrix"));
+  ctx->hs_c = ctx->tc;
+  ctx->hs_d = ctx->td;
+  ctx->hs_valid = true;
+  ctx->hs32_valid = need32 || (same && ctx->hs32_valid);
+  return PFE_OK;
+}
+
+pfe_status ensure_filter(pfe_ctx *ctx) {
+  if (ctx->has_filter) return PFE_OK;
+  if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
+  PFE_TRY(ensure_lmax(ctx));
+  ctx->xi = (ctx->a - ctx->tc) / ctx->td;
+  ctx->eta = (ctx->b - ctx->tc) / ctx->td;
+  ctx->eps = ctx->p_eps_frac * (ctx->eta - ctx->xi);
+  int32_t m = ctx->p_degree;
+  if (m <= 0) {
+    m = choose_degree(ctx->xi, ctx->eta, ctx->eps, ctx->p_rate, ctx->p_damping, 60000);
+    if (m < 0) return pfe_fail(ctx, PFE_E_ARG, "no filter degree <= 60000 meets the rate; widen eps or r");
+  }
+  std::vector<double> gam, g;
+  pq_coefficients(ctx->xi, ctx->eta, ctx->eps, m, gam);
+  damping_factors(ctx->p_damping, m, g);
+  ctx->coef.resize((size_t)m + 1);
+  for (int32_t j = 0; j <= m; ++j) ctx->coef[j] = gam[j] * g[j];
+  ctx->m = m;
+  ctx->has_filter = true;
+  return PFE_OK;
+}
+
+// Stochastic trace estimate of the number of eigenvalues in [lo, hi] (Sec. 2.4):
+// T_M = (n / M) sum_l v_l^T psi(Ht) v_l with normalised Philox-Gaussian v_l (stream 2).
+pfe_status estimate_count(pfe_ctx *ctx, double lo, double hi, double *out) {
+  PFE_TRY(ensure_hs(ctx, false));
+  const int64_t n = ctx->n;
+  const int32_t M = std::max(ctx->p_count_m, 1), deg = std::max(ctx->p_count_degree, 0);
+  const int64_t ld = round_up(M, 2);
+  cudaStream_t s = ctx->stream;
+  RESERVE(double, V, ctx->w_X, (size_t)n * ld);
+  RESERVE(double, Y, ctx->w_Y, (size_t)n * ld);
+  RESERVE(double, b0, ctx->w_T0, (size_t)n * ld);
+  RESERVE(double, b1, ctx->w_T1, (size_t)n * ld);
+  RESERVE(double, dots, ctx->w_small, (size_t)2 * M);
+  RESERVE(double, red, ctx->w_red, colreduce_work(n, M));
+  launch_zero<double>(V, n * ld, s);
+  launch_fill_normal<double>(ctx->p_seed, 2u, n, M, 0, V, ld, s);
+  launch_col_dots<double>(n, M, V, ld, V, ld, dots, red, s);
+  std::vector<double> nrm(M);
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(nrm.data(), dots, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  for (auto &v : nrm) v = 1.0 / std::sqrt(v);
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(dots + M, nrm.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s));
+  launch_scale_cols<double>(n, M, V, ld, dots + M, s);
+  const double xi = (lo - ctx->tc) / ctx->td, eta = (hi - ctx->tc) / ctx->td;
+  std::vector<double> gam, g;
+  chi_coefficients(xi, eta, deg, gam);
+  damping_factors(ctx->p_count_damping, deg, g);
+  for (int32_t j = 0; j <= deg; ++j) gam[j] *= g[j];
+  PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), gam.data(), deg, M, ld, V, Y, b0, b1, s));
+  launch_col_dots<double>(n, M, V, ld, Y, ld, dots, red, s);
+  std::vector<double> vy(M);
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(vy.data(), dots, sizeof(double) * M, cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  double sum = 0.0;
+  for (double v : vy) sum += v;
+  *out = (double)n / (double)M * sum;
+  return PFE_OK;
+}
+
+pfe_status count_estimate(pfe_ctx *ctx) {
+  if (ctx->has_count) return PFE_OK;
+  if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
+  PFE_TRY(ensure_lmax(ctx));
+  PFE_TRY(estimate_count(ctx, ctx->a, ctx->b, &ctx->count_est));
+  ctx->has_count = true;
+  return PFE_OK;
+}
+
+// The filter needs a subspace at least as wide as the number of eigenvalues in the margin
+// window [xi - eps, eta + eps] (Sec. 2.6): estimate that count too.
+pfe_status window_estimate(pfe_ctx *ctx, double *out) {
+  PFE_TRY(ensure_filter(ctx));
+  const double lo = ctx->tc + ctx->td * (ctx->xi - ctx->eps), hi = ctx->tc + ctx->td * (ctx->eta + ctx->eps);
+  return estimate_count(ctx, std::max(lo, ctx->p_lambda_min), std::min(hi, ctx->lmax), out);
+}
+
+// ---------------------------------------------------------------- CholQR2 (+ shifted retry)
+// Y (row-major n x k, row stride ld) <- Y R^{-1} with R^T R = Y^T Y; repeated passes.
+pfe_status cholqr(pfe_ctx *ctx, double *Y, int32_t k, int64_t ld, bool *broke) {
+  const int64_t n = ctx->n;
+  RESERVE(double, G, ctx->w_small, (size_t)k * k);
+  RESERVE(int, info, ctx->w_info, 4);
+  int lwork = 0;
+  PFE_SOLVER_TRY(ctx, cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, &lwork));
+  RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lwork, 1));
+  const double one = 1.0, zero = 0.0;
+  // G = Y^T Y: in column-major terms Y is Yc (k x n, ld) and G = Yc Yc^T
+  PFE_BLAS_TRY(ctx, cublasDsyrk(ctx->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, Y, (int)ld, &zero, G, k));
+  PFE_SOLVER_TRY(ctx, cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, work, lwork, info));
+  int hinfo = 0;
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  *broke = false;
+  if (hinfo != 0) {
+    // shifted CholeskyQR (Fukaya et al. 2020): G + s I with s = 11 (n k + k (k + 1)) u ||Y||^2
+    *broke = true;
+    PFE_BLAS_TRY(ctx, cublasDsyrk(ctx->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, Y, (int)ld, &zero, G, k));
+    std::vector<double> hG((size_t)k * k);
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double tr = 0.0;
+    for (int32_t i = 0; i < k; ++i) tr += hG[(size_t)i * k + i];
+    const double sh = 11.0 * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
+    for (int32_t i = 0; i < k; ++i) hG[(size_t)i * k + i] += sh;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(G, hG.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, ctx->stream));
+    PFE_SOLVER_TRY(ctx, cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, work, lwork, info));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hinfo != 0) return pfe_fail(ctx, PFE_E_BREAKDOWN, "CholeskyQR broke down even with a shift");
+  }
+  // Y R^{-1}: Yc <- R^{-T} Yc
+  PFE_BLAS_TRY(ctx, cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, k,
+                                (int)n, &one, G, k, Y, (int)ld));
+  return PFE_OK;
+}
+
+pfe_status cholqr2(pfe_ctx *ctx, double *Y, int32_t k, int64_t ld) {
+  if (k <= 0) return PFE_OK;
+  bool broke = false;
+  PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
+  PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
+  if (broke) PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
+  return PFE_OK;
+}
+
+// Y <- Y - L (L^T Y), twice (classical Gram-Schmidt against the locked block)
+pfe_status project_out(pfe_ctx *ctx, const double *L, int32_t nl, double *Y, int32_t k, int64_t ld) {
+  if (nl <= 0 || k <= 0) return PFE_OK;
+  const int64_t n = ctx->n;
+  RESERVE(double, h, ctx->w_small2, (size_t)nl * k);
+  const double one = 1.0, zero = 0.0, mone = -1.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, nl, k, (int)n, &one, L, (int)ld, Y, (int)ld,
+                                  &zero, h, nl));
+    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, nl, &mone, h, nl, L, (int)ld, &one, Y,
+                                  (int)ld));
+  }
+  return PFE_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+pfe_status pfe_springs_to_bsr(int32_t n_atoms, int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *k,
+                              const double *rhat, int64_t cap_nnzb, int32_t *row_ptr, int32_t *col_idx, double *vals,
+                              int64_t *nnzb) {
+  if (n_atoms < 1 || nbonds < 0 || !nnzb) return PFE_E_ARG;
+  if (nbonds > 0 && (!bi || !bj || !k || !rhat)) return PFE_E_ARG;
+  for (int64_t e = 0; e < nbonds; ++e) {
+    if (bi[e] < 0 || bi[e] >= n_atoms || bj[e] < 0 || bj[e] >= n_atoms || bi[e] == bj[e]) return PFE_E_ARG;
+    if (!std::isfinite(k[e]) || !std::isfinite(rhat[3 * e]) || !std::isfinite(rhat[3 * e + 1]) ||
+        !std::isfinite(rhat[3 * e + 2]))
+      return PFE_E_ARG;
+  }
+  // neighbour lists (both directions), sorted by (neighbour, bond)
+  std::vector<int64_t> off((size_t)n_atoms + 1, 0);
+  for (int64_t e = 0; e < nbonds; ++e) {
+    ++off[bi[e] + 1];
+    ++off[bj[e] + 1];
+  }
+  for (int32_t i = 0; i < n_atoms; ++i) off[i + 1] += off[i];
+  std::vector<std::pair<int32_t, int64_t>> nb((size_t)off[n_atoms]);
+  {
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    for (int64_t e = 0; e < nbonds; ++e) {
+      nb[pos[bi[e]]++] = {bj[e], e};
+      nb[pos[bj[e]]++] = {bi[e], e};
+    }
+  }
+  int64_t total = 0;
+  for (int32_t i = 0; i < n_atoms; ++i) {
+    std::sort(nb.begin() + off[i], nb.begin() + off[i + 1]);
+    int64_t uniq = 0;
+    for (int64_t t = off[i]; t < off[i + 1]; ++t)
+      if (t == off[i] || nb[t].first != nb[t - 1].first) ++uniq;
+    total += uniq + 1;
+  }
+  *nnzb = total;
+  if (total > INT32_MAX) return PFE_E_ARG;
+  if (cap_nnzb < total || !row_ptr || !col_idx || !vals) return PFE_E_CAPACITY;
+  int64_t p = 0;
+  auto rr = [&](int64_t e, int a, int b) {  // r_a r_b, symmetric in (a, b) bit for bit
+    const double *r = rhat + 3 * e;
+    return a <= b ? r[a] * r[b] : r[b] * r[a];
+  };
+  for (int32_t i = 0; i < n_atoms; ++i) {
+    row_ptr[i] = (int32_t)p;
+    double D[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t t = off[i]; t < off[i + 1]; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) D[3 * a + b] += k[nb[t].second] * rr(nb[t].second, a, b);
+    bool diag_done = false;
+    int64_t t = off[i];
+    while (t <= off[i + 1]) {
+      const bool end = (t == off[i + 1]);
+      if (!diag_done && (end || nb[t].first > i)) {
+        col_idx[p] = i;
+        std::memcpy(vals + 9 * p, D, sizeof(D));
+        ++p;
+        diag_done = true;
+      }
+      if (end) break;
+      const int32_t j = nb[t].first;
+      double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      while (t < off[i + 1] && nb[t].first == j) {
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) B[3 * a + b] -= k[nb[t].second] * rr(nb[t].second, a, b);
+        ++t;
+      }
+      col_idx[p] = j;
+      std::memcpy(vals + 9 * p, B, sizeof(B));
+      ++p;
+    }
+  }
+  row_ptr[n_atoms] = (int32_t)p;
+  return PFE_OK;
+}
+
+pfe_status pfe_create(pfe_ctx **out, int32_t n_atoms, int64_t nnzb, const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *vals, const double *masses, uint32_t flags, void *cuda_stream) {
+  if (!out) return PFE_E_ARG;
+  *out = nullptr;
+  if (n_atoms < 1 || nnzb < n_atoms || nnzb > INT32_MAX || !row_ptr || !col_idx || !vals) return PFE_E_ARG;
+  const bool dev = (flags & PFE_DEVICE_PTRS) != 0;
+  std::vector<int32_t> rp((size_t)n_atoms + 1), ci((size_t)nnzb);
+  std::vector<double> dv((size_t)9 * nnzb), ms;
+  auto fetch = [&](void *dst, const void *src, size_t bytes) -> bool {
+    if (!dev) {
+      std::memcpy(dst, src, bytes);
+      return true;
+    }
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+  };
+  if (!fetch(rp.data(), row_ptr, rp.size() * 4) || !fetch(ci.data(), col_idx, ci.size() * 4) ||
+      !fetch(dv.data(), vals, dv.size() * 8))
+    return PFE_E_CUDA;
+  if (masses) {
+    ms.resize((size_t)n_atoms);
+    if (!fetch(ms.data(), masses, ms.size() * 8)) return PFE_E_CUDA;
+    for (double m : ms)
+      if (!(m > 0.0) || !std::isfinite(m)) return PFE_E_ARG;
+  }
+  // structure checks
+  if (rp[0] != 0 || rp[n_atoms] != nnzb) return PFE_E_ARG;
+  double vmax = 0.0;
+  for (int32_t i = 0; i < n_atoms; ++i) {
+    if (rp[i + 1] < rp[i]) return PFE_E_ARG;
+    bool has_diag = false;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] < 0 || ci[p] >= n_atoms) return PFE_E_ARG;
+      if (p > rp[i] && ci[p] <= ci[p - 1]) return PFE_E_ARG;
+      if (ci[p] == i) has_diag = true;
+    }
+    if (!has_diag) return PFE_E_ARG;
+  }
+  for (double v : dv) {
+    if (!std::isfinite(v)) return PFE_E_ARG;
+    vmax = std::max(vmax, std::fabs(v));
+  }
+  if (!(flags & PFE_SKIP_SYM_CHECK)) {
+    const double tol = 1e-12 * vmax;
+    for (int32_t i = 0; i < n_atoms; ++i)
+      for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int32_t j = ci[p];
+        if (j < i) continue;
+        const int32_t *lo = ci.data() + rp[j], *hi = ci.data() + rp[j + 1];
+        const int32_t *f = std::lower_bound(lo, hi, i);
+        if (f == hi || *f != i) return PFE_E_NOTSYM;
+        const int64_t q = f - ci.data();
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            if (std::fabs(dv[9 * (size_t)p + 3 * a + b] - dv[9 * (size_t)q + 3 * b + a]) > tol) return PFE_E_NOTSYM;
+      }
+  }
+  pfe_ctx *ctx = new (std::nothrow) pfe_ctx();
+  if (!ctx) return PFE_E_NOMEM;
+  ctx->N = n_atoms;
+  ctx->n = 3 * (int64_t)n_atoms;
+  ctx->nnzb = nnzb;
+  ctx->has_mass = masses != nullptr;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](pfe_status s) {
+    pfe_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(PFE_E_CUDA);
+  if (cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) return bail(PFE_E_CUDA);
+  if (cublasSetStream(ctx->blas, ctx->stream) != CUBLAS_STATUS_SUCCESS) return bail(PFE_E_CUDA);
+  if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) return bail(PFE_E_CUDA);
+  if (cusolverDnSetStream(ctx->solver, ctx->stream) != CUSOLVER_STATUS_SUCCESS) return bail(PFE_E_CUDA);
+  DBuf delta;
+  if (dbuf_reserve(ctx->rp, rp.size() * 4) || dbuf_reserve(ctx->ci, ci.size() * 4) ||
+      dbuf_reserve(ctx->H, dv.size() * 8) || dbuf_reserve(delta, dv.size() * 8))
+    return bail(PFE_E_NOMEM);
+  cudaStream_t s = ctx->stream;
+  if (cudaMemcpyAsync(ctx->rp.p, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(ctx->ci.p, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, s) ||
+      cudaMemcpyAsync(masses ? delta.p : ctx->H.p, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice, s)) {
+    dbuf_free(delta);
+    return bail(PFE_E_CUDA);
+  }
+  if (masses) {
+    if (dbuf_reserve(ctx->mass, ms.size() * 8) ||
+        cudaMemcpyAsync(ctx->mass.p, ms.data(), ms.size() * 8, cudaMemcpyHostToDevice, s)) {
+      dbuf_free(delta);
+      return bail(PFE_E_NOMEM);
+    }
+    launch_mass_weight(n_atoms, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), delta.as<double>(), ctx->mass.as<double>(),
+                       ctx->H.as<double>(), s);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  dbuf_free(delta);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return bail(PFE_E_CUDA);
+  *out = ctx;
+  return PFE_OK;
+}
+
+void pfe_destroy(pfe_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  DBuf *bufs[] = {&ctx->rp, &ctx->ci, &ctx->H, &ctx->mass, &ctx->Hs64, &ctx->Hs32, &ctx->L, &ctx->w_X, &ctx->w_Y,
+                  &ctx->w_W, &ctx->w_T0, &ctx->w_T1, &ctx->w_T2, &ctx->w_small, &ctx->w_small2, &ctx->w_red,
+                  &ctx->w_idx, &ctx->w_cs_work, &ctx->w_info, &ctx->w_f32a, &ctx->w_f32b, &ctx->w_f32c,
+                  &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr};
+  for (DBuf *b : bufs) dbuf_free(*b);
+  if (ctx->blas) cublasDestroy(ctx->blas);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  delete ctx;
+}
+
+const char *pfe_last_error(const pfe_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
+  if (!ctx) return PFE_E_ARG;
+  if (!std::isfinite(v)) return pfe_fail(ctx, PFE_E_ARG, "parameter value must be finite");
+  auto int_ok = [&](double lo) { return v >= lo && v == std::floor(v) && v < 2147483647.0; };
+  switch (key) {
+    case PFE_P_DEGREE:
+      if (!int_ok(0)) return pfe_fail(ctx, PFE_E_ARG, "DEGREE must be an integer >= 0");
+      ctx->p_degree = (int32_t)v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_EPS_FRAC:
+      if (!(v > 0)) return pfe_fail(ctx, PFE_E_ARG, "EPS_FRAC must be > 0");
+      ctx->p_eps_frac = v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_RATE:
+      if (!(v > 0 && v < 1)) return pfe_fail(ctx, PFE_E_ARG, "RATE must be in (0, 1)");
+      ctx->p_rate = v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_DAMPING:
+      if (!(v == 0 || v == 1 || v == 2)) return pfe_fail(ctx, PFE_E_ARG, "DAMPING must be 0, 1 or 2");
+      ctx->p_damping = (int)v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_WIDTH:
+      if (!int_ok(0)) return pfe_fail(ctx, PFE_E_ARG, "WIDTH must be an integer >= 0");
+      ctx->p_width = (int32_t)v;
+      break;
+    case PFE_P_WIDTH_FACTOR:
+      if (!(v >= 1.0)) return pfe_fail(ctx, PFE_E_ARG, "WIDTH_FACTOR must be >= 1");
+      ctx->p_width_factor = v;
+      break;
+    case PFE_P_TOL:
+      if (!(v > 0)) return pfe_fail(ctx, PFE_E_ARG, "TOL must be > 0");
+      ctx->p_tol = v;
+      break;
+    case PFE_P_PRECISION:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "PRECISION must be 0 or 1");
+      ctx->p_precision = (int)v;
+      break;
+    case PFE_P_MAX_ITERS:
+      if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "MAX_ITERS must be an integer >= 1");
+      ctx->p_max_iters = (int32_t)v;
+      break;
+    case PFE_P_SEED:
+      if (!(v >= 0 && v == std::floor(v) && v < 9007199254740992.0)) return pfe_fail(ctx, PFE_E_ARG, "SEED must be a non-negative integer");
+      ctx->p_seed = (uint64_t)v;
+      ctx->has_count = false;
+      if (ctx->p_lambda_max <= 0) ctx->has_lmax = ctx->has_filter = false;
+      break;
+    case PFE_P_LAMBDA_MAX:
+      if (!(v >= 0)) return pfe_fail(ctx, PFE_E_ARG, "LAMBDA_MAX must be >= 0");
+      ctx->p_lambda_max = v;
+      ctx->has_lmax = ctx->has_filter = ctx->has_count = false;
+      break;
+    case PFE_P_LAMBDA_MIN:
+      ctx->p_lambda_min = v;
+      ctx->has_lmax = ctx->has_filter = ctx->has_count = false;
+      break;
+    case PFE_P_COUNT_M:
+      if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "COUNT_M must be an integer >= 1");
+      ctx->p_count_m = (int32_t)v;
+      ctx->has_count = false;
+      break;
+    case PFE_P_COUNT_DEGREE:
+      if (!int_ok(0)) return pfe_fail(ctx, PFE_E_ARG, "COUNT_DEGREE must be an integer >= 0");
+      ctx->p_count_degree = (int32_t)v;
+      ctx->has_count = false;
+      break;
+    case PFE_P_LANCZOS_STEPS:
+      if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "LANCZOS_STEPS must be an integer >= 1");
+      ctx->p_lanczos_steps = (int32_t)v;
+      if (ctx->p_lambda_max <= 0) ctx->has_lmax = ctx->has_filter = ctx->has_count = false;
+      break;
+    case PFE_P_COUNT_DAMPING:
+      if (!(v == 0 || v == 1 || v == 2)) return pfe_fail(ctx, PFE_E_ARG, "COUNT_DAMPING must be 0, 1 or 2");
+      ctx->p_count_damping = (int)v;
+      ctx->has_count = false;
+      break;
+    case PFE_P_MIN_WIDTH:
+      if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "MIN_WIDTH must be an integer >= 1");
+      ctx->p_min_width = (int32_t)v;
+      break;
+    case PFE_P_REFINE_TOL:
+      if (!(v > 0)) return pfe_fail(ctx, PFE_E_ARG, "REFINE_TOL must be > 0");
+      ctx->p_refine_tol = v;
+      break;
+    default:
+      return pfe_fail(ctx, PFE_E_ARG, "unknown parameter key " + std::to_string(key));
+  }
+  return PFE_OK;
+}
+
+pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
+  if (!ctx || !v) return PFE_E_ARG;
+  switch (key) {
+    case PFE_P_DEGREE: *v = ctx->p_degree; break;
+    case PFE_P_EPS_FRAC: *v = ctx->p_eps_frac; break;
+    case PFE_P_RATE: *v = ctx->p_rate; break;
+    case PFE_P_DAMPING: *v = ctx->p_damping; break;
+    case PFE_P_WIDTH: *v = ctx->p_width; break;
+    case PFE_P_WIDTH_FACTOR: *v = ctx->p_width_factor; break;
+    case PFE_P_TOL: *v = ctx->p_tol; break;
+    case PFE_P_PRECISION: *v = ctx->p_precision; break;
+    case PFE_P_MAX_ITERS: *v = ctx->p_max_iters; break;
+    case PFE_P_SEED: *v = (double)ctx->p_seed; break;
+    case PFE_P_LAMBDA_MAX: *v = ctx->p_lambda_max; break;
+    case PFE_P_LAMBDA_MIN: *v = ctx->p_lambda_min; break;
+    case PFE_P_COUNT_M: *v = ctx->p_count_m; break;
+    case PFE_P_COUNT_DEGREE: *v = ctx->p_count_degree; break;
+    case PFE_P_LANCZOS_STEPS: *v = ctx->p_lanczos_steps; break;
+    case PFE_P_COUNT_DAMPING: *v = ctx->p_count_damping; break;
+    case PFE_P_MIN_WIDTH: *v = ctx->p_min_width; break;
+    case PFE_P_REFINE_TOL: *v = ctx->p_refine_tol; break;
+    default: return PFE_E_ARG;
+  }
+  return PFE_OK;
+}
+
+pfe_status pfe_set_interval(pfe_ctx *ctx, double a, double b) {
+  if (!ctx) return PFE_E_ARG;
+  if (!std::isfinite(a) || !std::isfinite(b) || !(a < b) || a < 0)
+    return pfe_fail(ctx, PFE_E_ARG, "interval must satisfy 0 <= a < b");
+  ctx->a = a;
+  ctx->b = b;
+  ctx->has_interval = true;
+  ctx->has_filter = ctx->has_count = false;
+  return PFE_OK;
+}
+
+pfe_status pfe_estimate(pfe_ctx *ctx, double *lambda_max, double *count_est) {
+  if (!ctx) return PFE_E_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  PFE_TRY(ensure_lmax(ctx));
+  if (lambda_max) *lambda_max = ctx->lmax;
+  if (count_est) {
+    if (ctx->has_interval) {
+      PFE_TRY(count_estimate(ctx));
+      *count_est = ctx->count_est;
+    } else {
+      *count_est = std::nan("");
+    }
+  }
+  return PFE_OK;
+}
+
+pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs, double *c, double *d) {
+  if (!ctx) return PFE_E_ARG;
+  PFE_TRY(ensure_filter(ctx));
+  if (m) *m = ctx->m;
+  if (c) *c = ctx->tc;
+  if (d) *d = ctx->td;
+  if (coeffs) {
+    if (cap < ctx->m + 1) return pfe_fail(ctx, PFE_E_CAPACITY, "coefficient buffer too small");
+    std::copy(ctx->coef.begin(), ctx->coef.end(), coeffs);
+  }
+  return PFE_OK;
+}
+
+pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
+  if (!ctx) return PFE_E_ARG;
+  if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  const double t_start = now_s();
+  ctx->has_result = false;
+  ctx->n_found = 0;
+  ctx->stats = pfe_stats{};
+  const bool fp32 = ctx->p_precision == 1;
+  PFE_TRY(ensure_filter(ctx));
+  PFE_TRY(ensure_hs(ctx, fp32));
+  int32_t q = ctx->p_width;
+  double window_est = -1.0;
+  if (q <= 0) {
+    PFE_TRY(count_estimate(ctx));
+    PFE_TRY(window_estimate(ctx, &window_est));
+    const double qa = ctx->p_width_factor * std::max(ctx->count_est, 0.0);
+    const double qw = 1.1 * std::max(window_est, 0.0) + 8.0;
+    q = (int32_t)std::ceil(std::max(qa, qw));
+    q = std::max(q, ctx->p_min_width);
+  }
+  q = (int32_t)std::min<int64_t>(q, ctx->n);
+  const int64_t n = ctx->n, ld = round_up(q, 4);
+  ctx->ldq = ld;
+  cudaStream_t s = ctx->stream;
+  const size_t big = (size_t)n * ld;
+  RESERVE(double, X, ctx->w_X, big);
+  RESERVE(double, Y, ctx->w_Y, big);
+  RESERVE(double, W, ctx->w_W, big);
+  RESERVE(double, T0, ctx->w_T0, big);
+  RESERVE(double, T1, ctx->w_T1, big);
+  RESERVE(double, L, ctx->L, big);
+  RESERVE(double, A, ctx->w_rr, (size_t)q * q + (size_t)q + 8);
+  double *evals = A + (size_t)q * q;  // Ritz values from the dense eigensolver
+  RESERVE(double, red, ctx->w_red, colreduce_work(n, q) + (size_t)q + 8);
+  double *resid2 = red + colreduce_work(n, q);
+  RESERVE(int32_t, idx, ctx->w_idx, (size_t)q + 8);
+  RESERVE(int, info, ctx->w_info, 4);
+  float *X32 = nullptr, *Y32 = nullptr, *B32a = nullptr, *B32b = nullptr;
+  if (fp32) {
+    RESERVE(float, x32, ctx->w_f32a, big);
+    RESERVE(float, y32, ctx->w_f32b, big);
+    RESERVE(float, a32, ctx->w_f32c, big);
+    RESERVE(float, b32, ctx->w_f32d, big);
+    X32 = x32; Y32 = y32; B32a = a32; B32b = b32;
+    for (float *p : {X32, Y32, B32a, B32b}) launch_zero<float>(p, (int64_t)big, s);
+  }
+  for (double *p : {X, Y, W, T0, T1, L}) launch_zero<double>(p, (int64_t)big, s);
+
+  cudaEvent_t ev0, ev1, ev2, ev3;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  cudaEventCreate(&ev2);
+  cudaEventCreate(&ev3);
+  struct EvGuard {
+    cudaEvent_t *e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  };
+  cudaEvent_t evs[4] = {ev0, ev1, ev2, ev3};
+  EvGuard guard{evs};
+
+  // start block (stream 0 of the seeded Philox normals) and its orthonormalisation
+  launch_fill_normal<double>(ctx->p_seed, 0u, n, q, 0, X, ld, s);
+  PFE_TRY(check_launch(ctx, "start block"));
+  PFE_TRY(cholqr2(ctx, X, q, ld));
+
+  const double lmax = ctx->lmax, tol = ctx->p_tol;
+  int32_t act = q, nl = 0;
+  std::vector<double> lockLam, lockRes;
+  std::vector<double> hth(q), hr2(q);
+  int prev_count = -1, it = 0;
+  double prev_worst = 1e300;
+  pfe_status result = PFE_E_NOCONV;
+  bool use64 = !fp32;
+  int32_t fp64_sweeps = 0;
+  double t_filter = 0, t_orth = 0, t_rr = 0;
+  int64_t matvecs = 0;
+  for (it = 1; it <= ctx->p_max_iters; ++it) {
+    cudaEventRecord(ev0, s);
+    // ---- filter (Alg. 2) on the active columns
+    if (use64) {
+      PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, act, ld, X, Y, T0, T1, s));
+      ++fp64_sweeps;
+    } else {
+      launch_convert<double, float>(n, act, X, ld, X32, ld, s);
+      PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, act, ld, X32, Y32, B32a, B32b, s));
+      launch_convert<float, double>(n, act, Y32, ld, Y, ld, s);
+    }
+    matvecs += (int64_t)act * ctx->m;
+    cudaEventRecord(ev1, s);
+    // ---- orthonormalise against the locked vectors and within the block
+    PFE_TRY(project_out(ctx, L, nl, Y, act, ld));
+    PFE_TRY(cholqr2(ctx, Y, act, ld));
+    std::swap(X, Y);
+    cudaEventRecord(ev2, s);
+    // ---- Rayleigh-Ritz with H: W = H X, A = X^T W, A = Q Theta Q^T, X <- X Q, W <- W Q
+    launch_bsr_step<double>(bsr_H(ctx), MODE_SPMM, act, ld, X, nullptr, W, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+    PFE_TRY(check_launch(ctx, "H X"));
+    matvecs += act;
+    const double one = 1.0, zero = 0.0;
+    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, act, act, (int)n, &one, X, (int)ld, W, (int)ld,
+                                  &zero, A, act));
+    int lw = 0;
+    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, A,
+                                                    act, resid2, &lw));
+    RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
+    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, A, act,
+                                         evals, work, lw, info));
+    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, act, (int)n, act, &one, A, act, X, (int)ld, &zero,
+                                  Y, (int)ld));
+    std::swap(X, Y);
+    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, act, (int)n, act, &one, A, act, W, (int)ld, &zero,
+                                  T0, (int)ld));
+    std::swap(W, T0);
+    launch_col_resid2(n, act, W, X, ld, evals, resid2, red, s);
+    PFE_TRY(check_launch(ctx, "residuals"));
+    cudaEventRecord(ev3, s);
+    int hinfo = 0;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hth.data(), evals, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hr2.data(), resid2, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge (info " + std::to_string(hinfo) + ")");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    t_filter += ms * 1e-3;
+    cudaEventElapsedTime(&ms, ev1, ev2);
+    t_orth += ms * 1e-3;
+    cudaEventElapsedTime(&ms, ev2, ev3);
+    t_rr += ms * 1e-3;
+
+    // ---- convergence bookkeeping (before locking)
+    std::vector<double> rr(act);
+    double worst_unconv = 0.0;
+    int count_in = 0, unconv_in = 0;
+    for (double lv : lockLam)
+      if (lv >= ctx->a && lv <= ctx->b) ++count_in;
+    for (int32_t j = 0; j < act; ++j) {
+      rr[j] = std::sqrt(std::max(hr2[j], 0.0)) / lmax;
+      if (!std::isfinite(hth[j]) || !std::isfinite(rr[j]))
+        return pfe_fail(ctx, PFE_E_BREAKDOWN, "non-finite Ritz value or residual");
+      if (hth[j] > lmax * (1.0 + 1e-12)) return pfe_fail(ctx, PFE_E_BOUND, "a Ritz value exceeds the lambda_max bound");
+      if (hth[j] >= ctx->a && hth[j] <= ctx->b) {
+        ++count_in;
+        if (rr[j] > tol) {
+          ++unconv_in;
+          worst_unconv = std::max(worst_unconv, rr[j]);
+        }
+      }
+    }
+    // ---- lock converged pairs and compact the active block
+    std::vector<int32_t> lock_cols, keep_cols;
+    for (int32_t j = 0; j < act; ++j) {
+      if (rr[j] <= tol && nl + (int32_t)lock_cols.size() < q) lock_cols.push_back(j);
+      else keep_cols.push_back(j);
+    }
+    if (!lock_cols.empty()) {
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(idx, lock_cols.data(), sizeof(int32_t) * lock_cols.size(), cudaMemcpyHostToDevice, s));
+      launch_gather_cols(n, (int32_t)lock_cols.size(), X, ld, L + nl, ld, idx, s);
+      for (int32_t j : lock_cols) {
+        lockLam.push_back(hth[j]);
+        lockRes.push_back(rr[j]);
+      }
+      nl += (int32_t)lock_cols.size();
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(idx, keep_cols.data(), sizeof(int32_t) * std::max<size_t>(keep_cols.size(), 1),
+                                        cudaMemcpyHostToDevice, s));
+      launch_gather_cols(n, (int32_t)keep_cols.size(), X, ld, Y, ld, idx, s);
+      std::swap(X, Y);
+      PFE_TRY(check_launch(ctx, "locking"));
+      // the host vectors above must outlive the async copies
+      PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    }
+    act = (int32_t)keep_cols.size();
+    // FP32 filter: hand over to FP64 sweeps once the FP32 subspace stops improving
+    if (!use64 && (unconv_in == 0 || worst_unconv < ctx->p_refine_tol || worst_unconv > 0.5 * prev_worst)) use64 = true;
+    prev_worst = worst_unconv;
+    if ((unconv_in == 0 && count_in == prev_count && it >= 2) || act == 0) {
+      result = (count_in >= q) ? PFE_E_CAPACITY : PFE_OK;
+      break;
+    }
+    prev_count = count_in;
+  }
+  if (it > ctx->p_max_iters) it = ctx->p_max_iters;
+  // results: locked pairs inside [a, b], ascending
+  std::vector<int32_t> ord;
+  for (int32_t l = 0; l < nl; ++l)
+    if (lockLam[l] >= ctx->a && lockLam[l] <= ctx->b) ord.push_back(l);
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return lockLam[x] < lockLam[y]; });
+  ctx->result_cols = ord;
+  ctx->result_lam.clear();
+  ctx->result_res.clear();
+  double maxres = 0.0;
+  for (int32_t l : ord) {
+    ctx->result_lam.push_back(lockLam[l]);
+    ctx->result_res.push_back(lockRes[l] * lmax);
+    maxres = std::max(maxres, lockRes[l]);
+  }
+  ctx->n_found = (int32_t)ord.size();
+  ctx->has_result = true;
+  ctx->stats.iterations = it;
+  ctx->stats.width = q;
+  ctx->stats.degree = ctx->m;
+  ctx->stats.n_found = ctx->n_found;
+  ctx->stats.matvecs = matvecs;
+  ctx->stats.lambda_max = lmax;
+  ctx->stats.count_estimate = ctx->has_count ? ctx->count_est : -1.0;
+  ctx->stats.window_estimate = window_est;
+  ctx->stats.seconds_filter = t_filter;
+  ctx->stats.seconds_orth = t_orth;
+  ctx->stats.seconds_rr = t_rr;
+  ctx->stats.max_residual = maxres;
+  ctx->stats.fp64_sweeps = fp64_sweeps;
+  ctx->stats.status = (int32_t)result;
+  ctx->stats.seconds_total = now_s() - t_start;
+  if (n_found) *n_found = ctx->n_found;
+  if (result == PFE_E_CAPACITY) return pfe_fail(ctx, result, "every Ritz vector lies in [a, b]: raise PFE_P_WIDTH");
+  if (result == PFE_E_NOCONV) return pfe_fail(ctx, result, "iteration limit reached");
+  return PFE_OK;
+}
+
+pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *st) {
+  if (!ctx || !st) return PFE_E_ARG;
+  *st = ctx->stats;
+  return PFE_OK;
+}
+
+pfe_status pfe_get_eigenpairs(pfe_ctx *ctx, int32_t cap, double *lambda, double *vecs, double *resid, uint32_t flags) {
+  if (!ctx) return PFE_E_ARG;
+  if (!ctx->has_result) return pfe_fail(ctx, PFE_E_STATE, "no solve results");
+  const int32_t nf = ctx->n_found;
+  if (cap < nf) return pfe_fail(ctx, PFE_E_CAPACITY, "output capacity below the number of eigenpairs found");
+  if (lambda) std::copy(ctx->result_lam.begin(), ctx->result_lam.end(), lambda);
+  if (resid) std::copy(ctx->result_res.begin(), ctx->result_res.end(), resid);
+  if (vecs && nf > 0) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+    const int64_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    const int64_t ldt = round_up(nf, 4);
+    RESERVE(double, tmp, ctx->w_Y, (size_t)n * ldt);
+    RESERVE(int32_t, idx, ctx->w_idx, (size_t)nf);
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(idx, ctx->result_cols.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
+    launch_gather_cols(n, nf, ctx->L.as<double>(), ctx->ldq, tmp, ldt, idx, s);
+    if (flags & PFE_DEVICE_PTRS) {
+      launch_rowmajor_to_colmajor<double>(n, nf, tmp, ldt, vecs, n, s);
+    } else {
+      RESERVE(double, cm, ctx->w_W, (size_t)n * nf);
+      launch_rowmajor_to_colmajor<double>(n, nf, tmp, ldt, cm, n, s);
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(vecs, cm, sizeof(double) * n * nf, cudaMemcpyDeviceToHost, s));
+    }
+    PFE_TRY(check_launch(ctx, "eigenvector export"));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  }
+  return PFE_OK;
+}
+
+pfe_status pfe_filter_apply(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const void *X, int64_t ldx,
+                            void *Y, int64_t ldy, int dtype, void *stream) {
+  if (!ctx) return PFE_E_ARG;
+  if (k < 0 || (k > 0 && (!X || !Y)) || ldx < ctx->n || ldy < ctx->n || (dtype != PFE_F64 && dtype != PFE_F32))
+    return pfe_fail(ctx, PFE_E_ARG, "filter_apply: bad arguments");
+  if (coeffs && m < 0) return pfe_fail(ctx, PFE_E_ARG, "filter_apply: negative degree");
+  if (k == 0) return PFE_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  const double *cf = coeffs;
+  if (!cf) {
+    PFE_TRY(ensure_filter(ctx));
+    cf = ctx->coef.data();
+    m = ctx->m;
+  }
+  for (int32_t j = 0; j <= m; ++j)
+    if (!std::isfinite(cf[j])) return pfe_fail(ctx, PFE_E_ARG, "filter_apply: non-finite coefficient");
+  PFE_TRY(ensure_hs(ctx, dtype == PFE_F32));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  if (s != ctx->stream) PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // matrices built on ctx stream
+  const int64_t n = ctx->n, ld = round_up(k, 4);
+  const size_t big = (size_t)n * ld;
+  if (dtype == PFE_F64) {
+    RESERVE(double, Xr, ctx->w_X, big);
+    RESERVE(double, Yr, ctx->w_Y, big);
+    RESERVE(double, b0, ctx->w_T0, big);
+    RESERVE(double, b1, ctx->w_T1, big);
+    launch_colmajor_to_rowmajor<double>(n, k, static_cast<const double *>(X), ldx, Xr, ld, s);
+    PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), cf, m, k, ld, Xr, Yr, b0, b1, s));
+    launch_rowmajor_to_colmajor<double>(n, k, Yr, ld, static_cast<double *>(Y), ldy, s);
+  } else {
+    RESERVE(float, Xr, ctx->w_f32a, big);
+    RESERVE(float, Yr, ctx->w_f32b, big);
+    RESERVE(float, b0, ctx->w_f32c, big);
+    RESERVE(float, b1, ctx->w_f32d, big);
+    launch_colmajor_to_rowmajor<float>(n, k, static_cast<const float *>(X), ldx, Xr, ld, s);
+    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), cf, m, k, ld, Xr, Yr, b0, b1, s));
+    launch_rowmajor_to_colmajor<float>(n, k, Yr, ld, static_cast<float *>(Y), ldy, s);
+  }
+  return check_launch(ctx, "filter_apply");
+}
+
+pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const double *X, int64_t ldx,
+                              const double *Ybar, int64_t ldyb, double *Xbar, int64_t ldxb, double *vals_bar,
+                              void *stream) {
+  if (!ctx) return PFE_E_ARG;
+  if (k < 0 || (k > 0 && (!X || !Ybar || !Xbar)) || !vals_bar || ldx < ctx->n || ldyb < ctx->n || ldxb < ctx->n)
+    return pfe_fail(ctx, PFE_E_ARG, "filter_adjoint: bad arguments");
+  if (coeffs && m < 0) return pfe_fail(ctx, PFE_E_ARG, "filter_adjoint: negative degree");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  const double *cf = coeffs;
+  if (!cf) {
+    PFE_TRY(ensure_filter(ctx));
+    cf = ctx->coef.data();
+    m = ctx->m;
+  }
+  PFE_TRY(ensure_hs(ctx, false));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  if (s != ctx->stream) PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  launch_zero<double>(vals_bar, 9 * ctx->nnzb, s);
+  if (k == 0) return check_launch(ctx, "filter_adjoint");
+  const int64_t n = ctx->n, ld = round_up(k, 2);
+  const size_t vec = (size_t)n * ld;
+  // checkpoint spacing ~ sqrt(m): checkpoints hold (t_j0, t_{j0+1}) for j0 = 0, S, 2S, ...
+  const int32_t S = std::max<int32_t>(1, (int32_t)std::ceil(std::sqrt((double)std::max(m, 1))));
+  const int32_t nseg = (m + S - 1) / S;
+  // buffers: Xr, Ybr, 3 adjoint vectors, segment buffer of S + 1 vectors, checkpoints 2 * nseg
+  const size_t nvec = 2 + 3 + (size_t)(S + 1) + 2 * (size_t)std::max(nseg, 1);
+  RESERVE(double, base, ctx->w_ckpt, vec * nvec);
+  double *Xr = base, *Yb = base + vec, *a0 = base + 2 * vec, *a1 = base + 3 * vec, *a2 = base + 4 * vec;
+  double *seg = base + 5 * vec;
+  double *ck = seg + (size_t)(S + 1) * vec;
+  launch_zero<double>(base, (int64_t)(vec * nvec), s);
+  launch_colmajor_to_rowmajor<double>(n, k, X, ldx, Xr, ld, s);
+  launch_colmajor_to_rowmajor<double>(n, k, Ybar, ldyb, Yb, ld, s);
+  const Bsr<double> A = bsr_Hs64(ctx);
+  const double two_over_d = 2.0 / ctx->td;
+  auto tvec = [&](int32_t g, int which) { return ck + ((size_t)2 * g + which) * vec; };
+  // forward pass: t_0 .. t_{m-1}, storing (t_j0, t_{j0+1}) at every segment start j0 = g S
+  if (m >= 1) {
+    double *tp = seg, *tc = seg + vec;  // rolling (t_{j-1}, t_j)
+    launch_axpby<double>(n, k, 1.0, Xr, ld, 0.0, tp, ld, s);
+    launch_bsr_step<double>(A, MODE_SPMM, k, ld, Xr, nullptr, tc, nullptr, 0.5, 0.0, 0.0, 0.0, s);
+    launch_axpby<double>(n, k, 1.0, tp, ld, 0.0, tvec(0, 0), ld, s);
+    launch_axpby<double>(n, k, 1.0, tc, ld, 0.0, tvec(0, 1), ld, s);
+    for (int32_t j = 1; j + 1 < m; ++j) {
+      // t_{j+1} = A t_j - t_{j-1}, written over t_{j-1}
+      launch_bsr_step<double>(A, MODE_STEP, k, ld, tc, tp, tp, nullptr, 1.0, -1.0, 0.0, 0.0, s);
+      std::swap(tp, tc);  // (tp, tc) = (t_j, t_{j+1})
+      if (j % S == 0) {
+        launch_axpby<double>(n, k, 1.0, tp, ld, 0.0, tvec(j / S, 0), ld, s);
+        launch_axpby<double>(n, k, 1.0, tc, ld, 0.0, tvec(j / S, 1), ld, s);
+      }
+    }
+    if (m - 1 >= 1 && (m - 1) % S == 0) launch_axpby<double>(n, k, 1.0, tc, ld, 0.0, tvec((m - 1) / S, 0), ld, s);
+    PFE_TRY(check_launch(ctx, "adjoint forward"));
+  }
+  // reverse pass: a_m = g_m ybar; a_j = A a_{j+1} - a_{j+2} + g_j ybar (j >= 1);
+  // a_0 = A a_1 / 2 - a_2 + g_0 ybar; dL/dA += a_{j+1} t_j^T (j >= 1), + a_1 t_0^T / 2.
+  double *an2 = a2, *an1 = a1, *acur = a0;  // a_{j+2}, a_{j+1}, a_j
+  launch_zero<double>(an2, (int64_t)vec, s);
+  launch_axpby<double>(n, k, cf[m], Yb, ld, 0.0, an1, ld, s);  // a_m
+  for (int32_t g = nseg - 1; g >= 0 && m >= 1; --g) {
+    const int32_t j0 = g * S, j1 = std::min(m, j0 + S);  // this segment holds t_j0 .. t_{j1-1}
+    // recompute the segment from its checkpoint
+    launch_axpby<double>(n, k, 1.0, tvec(g, 0), ld, 0.0, seg, ld, s);
+    if (j1 - j0 > 1) launch_axpby<double>(n, k, 1.0, tvec(g, 1), ld, 0.0, seg + vec, ld, s);
+    for (int32_t j = j0 + 2; j < j1; ++j) {
+      double *out = seg + (size_t)(j - j0) * vec;
+      launch_bsr_step<double>(A, MODE_STEP, k, ld, seg + (size_t)(j - j0 - 1) * vec, seg + (size_t)(j - j0 - 2) * vec,
+                              out, nullptr, 1.0, -1.0, 0.0, 0.0, s);
+    }
+    for (int32_t j = j1 - 1; j >= j0; --j) {
+      const double *tj = seg + (size_t)(j - j0) * vec;
+      // outer products with a_{j+1}
+      launch_outer_accum<double>(A, k, ld, an1, tj, two_over_d * (j >= 1 ? 1.0 : 0.5), vals_bar, s);
+      // a_j
+      if (j >= 1)
+        launch_bsr_step<double>(A, MODE_ADJ, k, ld, an1, an2, acur, Yb, 1.0, -1.0, cf[j], 0.0, s);
+      else
+        launch_bsr_step<double>(A, MODE_ADJ, k, ld, an1, an2, acur, Yb, 0.5, -1.0, cf[0], 0.0, s);
+      double *t = an2;
+      an2 = an1;
+      an1 = acur;
+      acur = t;
+    }
+  }
+  // an1 now holds a_0 (or a_m = g_0 ybar for m == 0)
+  if (m == 0) launch_axpby<double>(n, k, cf[0], Yb, ld, 0.0, an1, ld, s);
+  launch_rowmajor_to_colmajor<double>(n, k, an1, ld, Xbar, ldxb, s);
+  return check_launch(ctx, "filter_adjoint");
+}
+
+pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *rhat,
+                             const double *vals_bar, double *k_bar, double *m_bar, void *stream) {
+  if (!ctx) return PFE_E_ARG;
+  if (!ctx->has_mass) return pfe_fail(ctx, PFE_E_STATE, "chain_springs needs a context created with masses");
+  if (nbonds < 0 || (nbonds > 0 && (!bi || !bj || !rhat || !k_bar)) || !vals_bar || !m_bar)
+    return pfe_fail(ctx, PFE_E_ARG, "chain_springs: bad arguments");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  launch_chain_springs(ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>(), ctx->mass.as<double>(),
+                       nbonds, bi, bj, rhat, vals_bar, k_bar, m_bar, s);
+  return check_launch(ctx, "chain_springs");
+}
+
+pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
+  if (!ctxs || nsamples < 0) return PFE_E_ARG;
+  pfe_status first = PFE_OK;
+  for (int32_t i = 0; i < nsamples; ++i) {
+    int32_t nf = 0;
+    pfe_status st = ctxs[i] ? pfe_solve(ctxs[i], &nf) : PFE_E_ARG;
+    if (n_found) n_found[i] = nf;
+    if (st != PFE_OK && first == PFE_OK) first = st;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+"""CPU tests of the C ABI boundary: the library loads, exports every declared entry point, and its
+host-side logic (BSR assembly, input validation) behaves as include/pfe.h states. No GPU compute."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import glassgen
+import oracle
+import paper_1902_07041_gb300 as pfe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pfe_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1902_07041_gb300 import build
+
+    build.build()
+    return pfe.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(pfe.EXPORTS)
+
+
+def test_springs_to_bsr_matches_oracle_hessian(lib):
+    g = glassgen.generate(80, 3)
+    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    N = g.n_atoms
+    assert rp[0] == 0 and rp[-1] == ci.size
+    D = np.zeros((3 * N, 3 * N))
+    for i in range(N):
+        cols = ci[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cols) > 0) and i in cols
+        for q in range(rp[i], rp[i + 1]):
+            D[3 * i:3 * i + 3, 3 * ci[q]:3 * ci[q] + 3] = vals[9 * q:9 * q + 9].reshape(3, 3)
+    assert np.array_equal(D, D.T)
+    s = np.repeat(1.0 / np.sqrt(g.mass), 3)
+    H = oracle.csr_from_springs(g).dense()
+    assert np.allclose(s[:, None] * D * s[None, :], H, rtol=0, atol=1e-15 * np.abs(H).max())
+
+
+def test_springs_to_bsr_rejects_bad_bonds(lib):
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_springs_to_bsr(4, [0, 1], [1, 1], [1.0, 1.0], np.ones((2, 3)) / np.sqrt(3))
+    assert e.value.status == pfe.PFE_E_ARG
+    with pytest.raises(pfe.PfeError):
+        pfe.pfe_springs_to_bsr(4, [0], [7], [1.0], np.ones((1, 3)))
+
+
+def test_duplicate_bonds_are_summed(lib):
+    r = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    rp, ci, v = pfe.pfe_springs_to_bsr(2, [0, 0], [1, 1], [1.0, 2.0], r)
+    assert list(rp) == [0, 2, 4] and list(ci) == [0, 1, 0, 1]
+    assert v[0] == 3.0 and v[9] == -3.0
+
+
+def _tiny():
+    g = glassgen.generate(20, 1)
+    return g, pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+
+
+def test_create_validates_inputs_on_host(lib):
+    g, (rp, ci, vals) = _tiny()
+    N = g.n_atoms
+    bad = vals.copy()
+    bad[9 * 1 + 1] += 1e-3  # breaks Delta_ij = Delta_ji^T
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_create(N, rp, ci, bad, g.mass)
+    assert e.value.status == pfe.PFE_E_NOTSYM
+    nanv = vals.copy()
+    nanv[5] = np.nan
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_create(N, rp, ci, nanv, g.mass)
+    assert e.value.status == pfe.PFE_E_ARG
+    badc = ci.copy()
+    badc[0] = N + 5
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_create(N, rp, badc, vals, g.mass)
+    assert e.value.status == pfe.PFE_E_ARG
+    m = g.mass.copy()
+    m[3] = -1.0
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_create(N, rp, ci, vals, m)
+    assert e.value.status == pfe.PFE_E_ARG
+    # a row without its diagonal block
+    rp2 = np.array([0, 1, 2], np.int32)
+    ci2 = np.array([1, 0], np.int32)
+    v2 = np.zeros(18)
+    with pytest.raises(pfe.PfeError) as e:
+        pfe.pfe_create(2, rp2, ci2, v2)
+    assert e.value.status == pfe.PFE_E_ARG
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.pfe_set_param(None, pfe.PFE_P_TOL, 1e-8) == pfe.PFE_E_ARG
+    assert lib.pfe_set_interval(None, 0.0, 1.0) == pfe.PFE_E_ARG
+    assert lib.pfe_solve(None, None) == pfe.PFE_E_ARG
+    lib.pfe_destroy(None)
