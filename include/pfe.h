@@ -162,6 +162,11 @@ typedef struct {
   int32_t fp64_sweeps; /* FP32 mode: iterations run with the FP64 filter */
   int32_t status;
   double window_estimate; /* estimated eigenvalue count of the margin window (automatic width only) */
+  int64_t kernel_launches;     /* launches of this library's own kernels during the solve */
+  int64_t filter_launches;     /* launches of the fused filter-step kernel inside the iteration */
+  int64_t filter_col_steps;    /* sum over those launches of their column counts (FP64 filter) */
+  int64_t filter_col_steps_f32;/* the same for the FP32 filter */
+  double seconds_filter_f32;   /* part of seconds_filter spent in FP32 filter sweeps */
 } pfe_stats;
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 

@@ -691,8 +691,9 @@ double or_count_estimate(const or_csr *H, double c, double d, double xi, double 
  *   W = H X; A = X^T W; A = Q Theta Q^T (Jacobi); X = X Q; W = W Q   (Rayleigh-Ritz, Alg. 1)
  *   r_i = ||w_i - theta_i x_i|| / lmax
  *   lock every pair with r_i <= tol.
- * Stop once no unconverged active Ritz value lies in [a, b], the number of pairs in [a, b]
- * (locked + active) equals that of the previous iteration, and at least two iterations ran.
+ * Stop once no unconverged active Ritz pair certifies an eigenvalue inside [a, b] (its residual
+ * interval [theta - r, theta + r] inside [a, b]), the number of converged pairs in [a, b] equals
+ * that of the previous iteration, and at least two iterations ran.
  *
  * Inputs: X0 (n x q, column-major).  Outputs (capacity cap): the pairs with eigenvalue in
  * [a, b], ascending, residuals relative to lmax.  Returns 0 on convergence, 1 if max_iter was
@@ -779,16 +780,18 @@ int or_si_solve(const or_csr *H, double a, double b, double lmin, double lmax, c
       }
       rr[j] = sqrt(s) / lmax;
     }
-    /* convergence bookkeeping before locking */
-    int32_t unconv_in = 0, count_in = 0, active_in = 0;
+    /* convergence bookkeeping: an unconverged Ritz pair (theta, r) certifies a not yet locked
+       eigenvalue in [a, b] only if [theta - r, theta + r] lies inside [a, b] (the Krylov-Weinstein
+       bound on the complement of the locked invariant subspace); other unconverged Ritz values in
+       [a, b] may be mixtures of eigenvectors from both sides of the interval */
+    int32_t unconv_in = 0, count_in = 0;
+    for (int32_t j = 0; j < act; ++j) {
+      double rabs = rr[j] * lmax;
+      if (rr[j] > tol && th[j] - rabs >= a && th[j] + rabs <= b) ++unconv_in;
+      if (rr[j] <= tol && th[j] >= a && th[j] <= b) ++count_in;
+    }
     for (int32_t l = 0; l < nl; ++l)
       if (Lam[l] >= a && Lam[l] <= b) ++count_in;
-    for (int32_t j = 0; j < act; ++j)
-      if (th[j] >= a && th[j] <= b) {
-        ++count_in;
-        ++active_in;
-        if (rr[j] > tol) ++unconv_in;
-      }
     /* lock converged pairs; compact the active block */
     int32_t keep = 0;
     for (int32_t j = 0; j < act; ++j) {
@@ -803,7 +806,6 @@ int or_si_solve(const or_csr *H, double a, double b, double lmin, double lmax, c
       }
     }
     act = keep;
-    (void)active_in;
     if ((unconv_in == 0 && count_in == prev_count && it >= 2) || act == 0) {
       status = (count_in >= q) ? 3 : 0;
       break;

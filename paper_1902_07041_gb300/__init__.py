@@ -52,7 +52,10 @@ class PfeStats(ctypes.Structure):
                 ("count_estimate", ctypes.c_double), ("seconds_total", ctypes.c_double),
                 ("seconds_filter", ctypes.c_double), ("seconds_orth", ctypes.c_double),
                 ("seconds_rr", ctypes.c_double), ("max_residual", ctypes.c_double),
-                ("fp64_sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("window_estimate", ctypes.c_double)]
+                ("fp64_sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("window_estimate", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
+                ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
+                ("seconds_filter_f32", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -149,16 +149,16 @@ void dispatch_mode(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X,
   const int64_t threads = (int64_t)A.n_atoms * nchunk * 32;
   const int64_t blocks = (threads + 255) / 256;
   if (mode == MODE_SPMM)
-    k_bsr_step<T, CPL, MODE_SPMM><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+    PFE_LAUNCH k_bsr_step<T, CPL, MODE_SPMM><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
                                                                   Z, Y, alpha, beta, g0, g1);
   else if (mode == MODE_FIRST)
-    k_bsr_step<T, CPL, MODE_FIRST><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X,
+    PFE_LAUNCH k_bsr_step<T, CPL, MODE_FIRST><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X,
                                                                    W, Z, Y, alpha, beta, g0, g1);
   else if (mode == MODE_ADJ)
-    k_bsr_step<T, CPL, MODE_ADJ><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+    PFE_LAUNCH k_bsr_step<T, CPL, MODE_ADJ><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
                                                                  Z, Y, alpha, beta, g0, g1);
   else
-    k_bsr_step<T, CPL, MODE_STEP><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
+    PFE_LAUNCH k_bsr_step<T, CPL, MODE_STEP><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
                                                                   Z, Y, alpha, beta, g0, g1);
 }
 
@@ -314,27 +314,27 @@ __global__ void k_outer_accum(int32_t n_atoms, const int32_t *__restrict__ rp, c
 void launch_mass_weight(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *delta, const double *mass,
                         double *H, cudaStream_t s) {
   const int64_t blocks = ((int64_t)n_atoms * 32 + 255) / 256;
-  k_mass_weight<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, delta, mass, H);
+  PFE_LAUNCH k_mass_weight<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, delta, mass, H);
 }
 
 void launch_filter_matrix(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha,
                           double shift, double *out64, float *out32, cudaStream_t s) {
   const int64_t blocks = ((int64_t)n_atoms * 32 + 255) / 256;
-  k_filter_matrix<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, H, alpha, shift, out64, out32);
+  PFE_LAUNCH k_filter_matrix<<<(unsigned)blocks, 256, 0, s>>>(n_atoms, rp, ci, H, alpha, shift, out64, out32);
 }
 
 void launch_chain_springs(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, const double *mass,
                           int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *rhat, const double *hbar,
                           double *kbar, double *mbar, cudaStream_t s) {
-  if (nbonds > 0) k_chain_k<<<(unsigned)((nbonds + 255) / 256), 256, 0, s>>>(rp, ci, mass, nbonds, bi, bj, rhat, hbar, kbar);
-  if (n_atoms > 0) k_chain_m<<<(unsigned)((n_atoms + 255) / 256), 256, 0, s>>>(n_atoms, rp, ci, H, mass, hbar, mbar);
+  if (nbonds > 0) PFE_LAUNCH k_chain_k<<<(unsigned)((nbonds + 255) / 256), 256, 0, s>>>(rp, ci, mass, nbonds, bi, bj, rhat, hbar, kbar);
+  if (n_atoms > 0) PFE_LAUNCH k_chain_m<<<(unsigned)((n_atoms + 255) / 256), 256, 0, s>>>(n_atoms, rp, ci, H, mass, hbar, mbar);
 }
 
 template <typename T>
 void launch_outer_accum(const Bsr<T> &pattern, int32_t k, int64_t ld, const T *A, const T *Tm, double alpha,
                         double *hbar, cudaStream_t s) {
   const int64_t blocks = ((int64_t)pattern.n_atoms * 32 + 255) / 256;
-  k_outer_accum<T><<<(unsigned)blocks, 256, 0, s>>>(pattern.n_atoms, pattern.rp, pattern.ci, k, ld, A, Tm, alpha, hbar);
+  PFE_LAUNCH k_outer_accum<T><<<(unsigned)blocks, 256, 0, s>>>(pattern.n_atoms, pattern.rp, pattern.ci, k, ld, A, Tm, alpha, hbar);
 }
 template void launch_outer_accum<double>(const Bsr<double> &, int32_t, int64_t, const double *, const double *, double,
                                          double *, cudaStream_t);

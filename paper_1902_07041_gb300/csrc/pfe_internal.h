@@ -15,6 +15,12 @@
 
 namespace pfe {
 
+// Number of kernels this library has launched (all of its own kernels; cuBLAS/cuSOLVER excluded).
+int64_t launch_count();
+void count_launch();
+// Prefix of every kernel launch statement in this library: counts it, then launches.
+#define PFE_LAUNCH ::pfe::count_launch(),
+
 // --------------------------------------------------------------------------------------
 // Device buffers
 // --------------------------------------------------------------------------------------

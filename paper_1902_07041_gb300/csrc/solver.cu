@@ -761,11 +761,15 @@ pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
   pfe_status result = PFE_E_NOCONV;
   bool use64 = !fp32;
   int32_t fp64_sweeps = 0;
-  double t_filter = 0, t_orth = 0, t_rr = 0;
-  int64_t matvecs = 0;
+  double t_filter = 0, t_filter32 = 0, t_orth = 0, t_rr = 0;
+  int64_t matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
+  const int64_t launches0 = launch_count();
   for (it = 1; it <= ctx->p_max_iters; ++it) {
     cudaEventRecord(ev0, s);
     // ---- filter (Alg. 2) on the active columns
+    const bool was64 = use64;
+    f_launch += std::max(ctx->m, 1);
+    (use64 ? f_cols64 : f_cols32) += (int64_t)act * std::max(ctx->m, 1);
     if (use64) {
       PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, act, ld, X, Y, T0, T1, s));
       ++fp64_sweeps;
@@ -812,12 +816,16 @@ pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ev0, ev1);
     t_filter += ms * 1e-3;
+    if (!was64) t_filter32 += ms * 1e-3;
     cudaEventElapsedTime(&ms, ev1, ev2);
     t_orth += ms * 1e-3;
     cudaEventElapsedTime(&ms, ev2, ev3);
     t_rr += ms * 1e-3;
 
-    // ---- convergence bookkeeping (before locking)
+    // ---- convergence bookkeeping.  Converged: r <= tol.  An unconverged pair blocks termination
+    // only when its residual interval [theta - r, theta + r] lies inside [a, b]: the Krylov-Weinstein
+    // bound then places a not yet locked eigenvalue in the interval.  Other unconverged Ritz values
+    // in [a, b] can be mixtures of eigenvectors from both sides and never converge.
     std::vector<double> rr(act);
     double worst_unconv = 0.0;
     int count_in = 0, unconv_in = 0;
@@ -828,12 +836,12 @@ pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
       if (!std::isfinite(hth[j]) || !std::isfinite(rr[j]))
         return pfe_fail(ctx, PFE_E_BREAKDOWN, "non-finite Ritz value or residual");
       if (hth[j] > lmax * (1.0 + 1e-12)) return pfe_fail(ctx, PFE_E_BOUND, "a Ritz value exceeds the lambda_max bound");
-      if (hth[j] >= ctx->a && hth[j] <= ctx->b) {
-        ++count_in;
-        if (rr[j] > tol) {
-          ++unconv_in;
-          worst_unconv = std::max(worst_unconv, rr[j]);
-        }
+      const double rabs = rr[j] * lmax;
+      if (rr[j] <= tol) {
+        if (hth[j] >= ctx->a && hth[j] <= ctx->b) ++count_in;
+      } else if (hth[j] - rabs >= ctx->a && hth[j] + rabs <= ctx->b) {
+        ++unconv_in;
+        worst_unconv = std::max(worst_unconv, rr[j]);
       }
     }
     // ---- lock converged pairs and compact the active block
@@ -893,6 +901,11 @@ pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
   ctx->stats.lambda_max = lmax;
   ctx->stats.count_estimate = ctx->has_count ? ctx->count_est : -1.0;
   ctx->stats.window_estimate = window_est;
+  ctx->stats.kernel_launches = launch_count() - launches0;
+  ctx->stats.filter_launches = f_launch;
+  ctx->stats.filter_col_steps = f_cols64;
+  ctx->stats.filter_col_steps_f32 = f_cols32;
+  ctx->stats.seconds_filter_f32 = t_filter32;
   ctx->stats.seconds_filter = t_filter;
   ctx->stats.seconds_orth = t_orth;
   ctx->stats.seconds_rr = t_rr;

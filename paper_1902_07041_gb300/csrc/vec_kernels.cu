@@ -2,9 +2,17 @@
 // deterministic column reductions (norms, dots, residual norms), column scaling and
 // gathers for locking, precision conversions and layout transposes for the C ABI.
 // Multivectors are row-major n x k with row stride ld unless a name says otherwise.
+#include <atomic>
+
 #include "pfe_internal.h"
 
 namespace pfe {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+int64_t launch_count() { return g_launches.load(); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes) {
   if (bytes <= b.bytes && b.p) return cudaSuccess;
@@ -184,7 +192,7 @@ template <typename T>
 void launch_fill_normal(uint64_t seed, uint32_t stream_id, int64_t n, int32_t k, int32_t col0, T *X, int64_t ld,
                         cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
-  k_fill_normal<T><<<grid1(n * k), 256, 0, s>>>(seed, stream_id, n, k, col0, X, ld);
+  PFE_LAUNCH k_fill_normal<T><<<grid1(n * k), 256, 0, s>>>(seed, stream_id, n, k, col0, X, ld);
 }
 template void launch_fill_normal<double>(uint64_t, uint32_t, int64_t, int32_t, int32_t, double *, int64_t, cudaStream_t);
 template void launch_fill_normal<float>(uint64_t, uint32_t, int64_t, int32_t, int32_t, float *, int64_t, cudaStream_t);
@@ -201,9 +209,9 @@ void launch_col_dots(int64_t n, int32_t k, const T *X, int64_t ldx, const T *Y, 
   const int32_t nblk = (int32_t)((n + kRowsPerBlock - 1) / kRowsPerBlock);
   if (nblk > 0) {
     dim3 g(nblk, (k + 255) / 256);
-    k_col_dots_partial<T><<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, work);
+    PFE_LAUNCH k_col_dots_partial<T><<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, work);
   }
-  k_col_finish<<<grid1(k), 256, 0, s>>>(nblk, k, work, out);
+  PFE_LAUNCH k_col_finish<<<grid1(k), 256, 0, s>>>(nblk, k, work, out);
 }
 template void launch_col_dots<double>(int64_t, int32_t, const double *, int64_t, const double *, int64_t, double *,
                                       double *, cudaStream_t);
@@ -216,15 +224,15 @@ void launch_col_resid2(int64_t n, int32_t k, const double *W, const double *X, i
   const int32_t nblk = (int32_t)((n + kRowsPerBlock - 1) / kRowsPerBlock);
   if (nblk > 0) {
     dim3 g(nblk, (k + 255) / 256);
-    k_col_resid_partial<<<g, 256, 0, s>>>(n, k, W, X, ld, theta, work);
+    PFE_LAUNCH k_col_resid_partial<<<g, 256, 0, s>>>(n, k, W, X, ld, theta, work);
   }
-  k_col_finish<<<grid1(k), 256, 0, s>>>(nblk, k, work, out);
+  PFE_LAUNCH k_col_finish<<<grid1(k), 256, 0, s>>>(nblk, k, work, out);
 }
 
 template <typename T>
 void launch_scale_cols(int64_t n, int32_t k, T *X, int64_t ld, const double *scale, cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
-  k_scale_cols<T><<<grid1(n * k), 256, 0, s>>>(n, k, X, ld, scale);
+  PFE_LAUNCH k_scale_cols<T><<<grid1(n * k), 256, 0, s>>>(n, k, X, ld, scale);
 }
 template void launch_scale_cols<double>(int64_t, int32_t, double *, int64_t, const double *, cudaStream_t);
 template void launch_scale_cols<float>(int64_t, int32_t, float *, int64_t, const double *, cudaStream_t);
@@ -232,7 +240,7 @@ template void launch_scale_cols<float>(int64_t, int32_t, float *, int64_t, const
 template <typename T>
 void launch_axpby(int64_t n, int32_t k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
-  k_axpby<T><<<grid1(n * k), 256, 0, s>>>(n, k, alpha, X, ldx, beta, Y, ldy);
+  PFE_LAUNCH k_axpby<T><<<grid1(n * k), 256, 0, s>>>(n, k, alpha, X, ldx, beta, Y, ldy);
 }
 template void launch_axpby<double>(int64_t, int32_t, double, const double *, int64_t, double, double *, int64_t,
                                    cudaStream_t);
@@ -242,7 +250,7 @@ template void launch_axpby<float>(int64_t, int32_t, float, const float *, int64_
 template <typename Tin, typename Tout>
 void launch_convert(int64_t n, int32_t k, const Tin *X, int64_t ldx, Tout *Y, int64_t ldy, cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
-  k_convert<Tin, Tout><<<grid1(n * k), 256, 0, s>>>(n, k, X, ldx, Y, ldy);
+  PFE_LAUNCH k_convert<Tin, Tout><<<grid1(n * k), 256, 0, s>>>(n, k, X, ldx, Y, ldy);
 }
 template void launch_convert<double, float>(int64_t, int32_t, const double *, int64_t, float *, int64_t, cudaStream_t);
 template void launch_convert<float, double>(int64_t, int32_t, const float *, int64_t, double *, int64_t, cudaStream_t);
@@ -250,20 +258,20 @@ template void launch_convert<float, double>(int64_t, int32_t, const float *, int
 void launch_gather_cols(int64_t n, int32_t kdst, const double *src, int64_t lds, double *dst, int64_t ldd,
                         const int32_t *idx, cudaStream_t s) {
   if (n <= 0 || kdst <= 0) return;
-  k_gather_cols<<<grid1(n * kdst), 256, 0, s>>>(n, kdst, src, lds, dst, ldd, idx);
+  PFE_LAUNCH k_gather_cols<<<grid1(n * kdst), 256, 0, s>>>(n, kdst, src, lds, dst, ldd, idx);
 }
 
 template <typename T>
 void launch_colmajor_to_rowmajor(int64_t n, int32_t k, const T *C, int64_t ldc, T *R, int64_t ldr, cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
   dim3 g((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
-  k_col_to_row<T><<<g, dim3(32, 8), 0, s>>>(n, k, C, ldc, R, ldr);
+  PFE_LAUNCH k_col_to_row<T><<<g, dim3(32, 8), 0, s>>>(n, k, C, ldc, R, ldr);
 }
 template <typename T>
 void launch_rowmajor_to_colmajor(int64_t n, int32_t k, const T *R, int64_t ldr, T *C, int64_t ldc, cudaStream_t s) {
   if (n <= 0 || k <= 0) return;
   dim3 g((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
-  k_row_to_col<T><<<g, dim3(32, 8), 0, s>>>(n, k, R, ldr, C, ldc);
+  PFE_LAUNCH k_row_to_col<T><<<g, dim3(32, 8), 0, s>>>(n, k, R, ldr, C, ldc);
 }
 template void launch_colmajor_to_rowmajor<double>(int64_t, int32_t, const double *, int64_t, double *, int64_t,
                                                   cudaStream_t);
