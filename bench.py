@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: time to all interval eigenpairs (residual <= 1e-8) of a synthetic glass Hessian,
+with the filter's SpMM throughput and the mixed-precision form beside the FP64 form.
+
+One step = one full solve through the C ABI: lambda_max bound, filter design, count estimate and
+the filtered subspace iteration (filter, CholQR2, Rayleigh-Ritz, residuals, locking) until every
+eigenpair in the interval has converged.  Inputs are seeded and synthetic (glassgen).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
+
+Under torchrun (N > 1) every rank solves its own replica (the single solve does not shard: replicas
+only); the value is the max over ranks of the per-step time.  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload and extrapolates to the solve's work.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to all interval eigenpairs (resid≤1e-8); filter SpMM GB/s; mixed vs FP64"
+
+# Workloads (binary glass of glassgen: density 0.06/A^3, RSA d_min 2.2 A, bonds r < 3.5 A,
+# k lognormal(1, 0.3), 64 % A / 36 % B).  The N = 100,000 interval keeps the lower edge
+# 0.02 lambda_max of the stated configuration and ends where it holds ~700 modes (598 found):
+# the literal upper edge 0.03 lambda_max holds ~4,980 modes for this generator.
+WORKLOADS = {
+    "glass-n100k-fp64": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=0),
+    "glass-n100k-mixed": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=1),
+    "glass-n1k-fp64": dict(N=1_000, seed=0, lo=0.02, hi=0.05, precision=0),
+}
+DEFAULT = "glass-n100k-fp64"
+
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def filter_work(n_atoms, nnzb, k, vec_bytes, val_bytes):
+    """Algorithmic bytes and flops of one fused Chebyshev step on k columns (one launch)."""
+    n = 3 * n_atoms
+    kt = 128 if vec_bytes == 4 else 64  # columns per warp (CPL x 32)
+    tiles = -(-k // kt)
+    byts = tiles * (nnzb * (9 * val_bytes + 4) + 4 * (n_atoms + 1)) + 5 * n * k * vec_bytes
+    flops = 18 * nnzb * k + 6 * n * k
+    return byts, flops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"pfe_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [x for x in sm if x > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(load or sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def make_problem(wl):
+    import glassgen
+    import paper_1902_07041_gb300 as pfe
+
+    g = glassgen.generate(wl["N"], wl["seed"])
+    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    return g, rp, ci, vals
+
+
+def one_step(pfe, torch, g, rp, ci, vals, wl, ev):
+    """create (H2D) -> [estimate + solve] -> eigenpairs to host (D2H) -> destroy.
+    ev = (e_start, e_solve0, e_solve1, e_end) CUDA events on the default stream."""
+    ev[0].record()
+    ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, wl["precision"])
+        torch.cuda.synchronize()
+        ev[1].record()
+        lmax, _ = pfe.pfe_estimate(ctx)
+        pfe.pfe_set_interval(ctx, wl["lo"] * lmax, wl["hi"] * lmax)
+        nf, _ = pfe.pfe_solve(ctx)
+        ev[2].record()
+        lam, vecs, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
+        stats = pfe.pfe_get_stats(ctx)
+    finally:
+        pfe.pfe_destroy(ctx)
+    ev[3].record()
+    torch.cuda.synchronize()
+    stats["h2d_bytes"] = rp.nbytes + ci.nbytes + vals.nbytes + g.mass.nbytes
+    stats["d2h_bytes"] = lam.nbytes + vecs.nbytes + res.nbytes
+    stats["max_rel_residual"] = float(res.max() / lmax) if nf else 0.0
+    stats["n_found"] = nf
+    return stats
+
+
+def oracle_sample(g, stats, budget_s=20.0):
+    """Oracle (FP64 CPU, single thread) on a bounded sample of the same workload: seconds per
+    single-vector Chebyshev product on this H and seconds per dense flop (Householder QR of an
+    n x 32 block), extrapolated to the solve's MatVec count and dense flop count."""
+    import numpy as np
+
+    import oracle
+
+    H = oracle.csr_from_springs(g)
+    n = H.n
+    X = oracle.normal_block(7, 0, n, 2)
+    m = 4
+    t0 = time.perf_counter()
+    oracle.cheb_filter(H, 0.5, 0.5, np.ones(m + 1) / (m + 1), X)
+    t_mv = (time.perf_counter() - t0) / (2 * m)
+    k = 32
+    Xq = oracle.normal_block(8, 0, n, k)
+    t0 = time.perf_counter()
+    oracle.householder_qr(Xq)
+    t_qr = time.perf_counter() - t0
+    sec_per_flop = t_qr / (4.0 * n * k * k)
+    width = stats["width"]
+    dense_flops = stats["iterations"] * 12.0 * n * width * width  # QR + RR + projections, per iteration
+    est = stats["matvecs"] * t_mv + dense_flops * sec_per_flop
+    sample = (f"oracle Alg. 2 on {2 * m} single-vector products of this H ({t_mv * 1e3:.1f} ms each) and a "
+              f"Householder QR of {n}x{k} ({t_qr:.2f} s), extrapolated to the GPU solve's "
+              f"{stats['matvecs']} MatVecs and ~{dense_flops:.3g} dense flops")
+    return est, sample
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    g, rp, ci, vals = make_problem(wl)
+    # the solve's work: MatVecs and width of the GPU form are not known here; use the oracle's own
+    # filter design for the same interval and the paper's iteration model (n_iter from stats file
+    # if present, else 13 iterations at width 1.6 x the count estimate).
+    import oracle
+
+    H = oracle.csr_from_springs(g)
+    th, rb, lmax = oracle.lanczos_lmax(H, 30, 0)
+    c = d = 0.5 * lmax
+    xi, eta = (wl["lo"] * lmax - c) / d, (wl["hi"] * lmax - c) / d
+    eps = 0.25 * (eta - xi)
+    m = oracle.select_degree(xi, eta, eps, 0.1 ** 0.5, "none")
+    cnt = oracle.count_estimate(H, c, d, xi, eta, 100, "none", 4, 0)  # 4 probe vectors keep it bounded
+    width = int(max(1.5 * cnt, 16))
+    iters = 13
+    stats = {"width": width, "iterations": iters, "matvecs": int(iters * 0.75 * width * m)}
+    times = []
+    est = sample = None
+    for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        est, sample = oracle_sample(g, stats)
+        times.append(time.perf_counter() - t0)
+    line = {"metric": METRIC, "value": est, "unit": "s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * est,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **wl, "degree": m, "width": width},
+            "cpu_baseline": {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample + f"; {iters} iterations at width {width}, degree {m} assumed"},
+            "e2e": {"value": est, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": times[-1]}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, wl):
+    import numpy as np
+    import torch
+
+    import paper_1902_07041_gb300 as pfe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pfe.load()
+    g, rp, ci, vals = make_problem(wl)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    evs = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(4)]  # noqa: E731
+    for _ in range(args.warmup):
+        one_step(pfe, torch, g, rp, ci, vals, wl, evs())
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    steps = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e = evs()
+        st = one_step(pfe, torch, g, rp, ci, vals, wl, e)
+        st["solve_s"] = e[1].elapsed_time(e[2]) / 1e3
+        st["e2e_s"] = e[0].elapsed_time(e[3]) / 1e3
+        steps.append(st)
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    solve_s = sum(s["solve_s"] for s in steps) / len(steps)
+    e2e_s = sum(s["e2e_s"] for s in steps) / len(steps)
+    if dist is not None:
+        t = torch.tensor([solve_s, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        solve_s, e2e_s = float(t[0]), float(t[1])
+    last = steps[-1]
+    # roofline of the dominant kernel (the fused filter step): FP64 is bound by the FP64 pipe
+    nnzb = int(ci.size)
+    hbm, hbm_src = peaks()
+    if last["filter_col_steps"] > 0:
+        secs64 = last["seconds_filter"] - last["seconds_filter_f32"]
+        _, fl = filter_work(g.n_atoms, nnzb, 1, 8, 8)
+        flops = fl * last["filter_col_steps"]
+        achieved = flops / secs64 / 1e12
+        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 8, 8)
+        roof = {"bound": "alu", "kernel": "k_bsr_step<double> (fused Chebyshev step)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
+                "filter_gbs_fp64": (b1 / last["width"]) * last["filter_col_steps"] / secs64 / 1e9,
+                "launches": last["filter_launches"]}
+    else:
+        secs32 = last["seconds_filter_f32"]
+        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 4, 4)
+        gbs = (b1 / last["width"]) * last["filter_col_steps_f32"] / secs32 / 1e9
+        roof = {"bound": "hbm", "kernel": "k_bsr_step<float>", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "traffic": None, "peak_source": hbm_src}
+    line = {
+        "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * solve_s, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == 0 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, **wl, "n": 3 * wl["N"], "nnzb": nnzb, "width": last["width"],
+                   "degree": last["degree"], "iterations": last["iterations"], "n_found": last["n_found"],
+                   "matvecs": last["matvecs"], "parallelism": f"replicas x{world}",
+                   "l2": "working set (multivectors of n x width) far above the 129 MB L2"},
+        "roofline": roof,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(last["h2d_bytes"]),
+                "d2h_bytes_per_step": int(last["d2h_bytes"])},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in steps)),
+        "clocks": clocks,
+        "breakdown_s": {"filter": last["seconds_filter"], "orth": last["seconds_orth"], "rr": last["seconds_rr"]},
+        "max_rel_residual": last["max_rel_residual"], "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, sample = oracle_sample(g, last)
+        line["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0 and args.mixed and wl["precision"] == 0:
+        wm = dict(wl, precision=1)
+        one_step(pfe, torch, g, rp, ci, vals, wm, evs())
+        e = evs()
+        sm = one_step(pfe, torch, g, rp, ci, vals, wm, e)
+        b1, _ = filter_work(g.n_atoms, nnzb, sm["width"], 4, 4)
+        gbs32 = (b1 / sm["width"]) * sm["filter_col_steps_f32"] / max(sm["seconds_filter_f32"], 1e-12) / 1e9
+        line["mixed"] = {"value": e[1].elapsed_time(e[2]) / 1e3, "unit": "s", "fp64_sweeps": sm["fp64_sweeps"],
+                         "iterations": sm["iterations"], "n_found": sm["n_found"],
+                         "max_rel_residual": sm["max_rel_residual"],
+                         "filter_f32": {"achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
+                                        "peak_source": hbm_src}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_native(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -162,11 +162,13 @@ typedef struct {
   int32_t fp64_sweeps; /* FP32 mode: iterations run with the FP64 filter */
   int32_t status;
   double window_estimate; /* estimated eigenvalue count of the margin window (automatic width only) */
-  int64_t kernel_launches;     /* launches of this library's own kernels during the solve */
+  int64_t kernel_launches;     /* launches of this library's own kernels since the context was created
+                                  (process-wide counter: exact when one context works at a time) */
   int64_t filter_launches;     /* launches of the fused filter-step kernel inside the iteration */
   int64_t filter_col_steps;    /* sum over those launches of their column counts (FP64 filter) */
   int64_t filter_col_steps_f32;/* the same for the FP32 filter */
   double seconds_filter_f32;   /* part of seconds_filter spent in FP32 filter sweeps */
+  int64_t batch_replays;       /* pfe_solve_batch: replays of the captured batched-filter graph */
 } pfe_stats;
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 
@@ -207,7 +209,12 @@ pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, co
  * ------------------------------------------------------------------------------------- */
 
 /* Solve every context's interval problem; n_found[s] per sample.  Each context must have its
- * interval set.  Returns the first failing status (the others still run). */
+ * interval set; all must live on one device.  The iterations of all samples advance in lockstep:
+ * the filter of every FP64 sample runs as one persistent kernel per Chebyshev step over all
+ * samples' work, captured once in a CUDA graph and replayed per iteration (its column tile and
+ * grid size chosen by timing the candidates on the first call); the dense steps run per sample.
+ * In the stats of every sample seconds_filter is the batch's shared filter time.
+ * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
 
 #ifdef __cplusplus

@@ -55,7 +55,7 @@ class PfeStats(ctypes.Structure):
                 ("fp64_sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("window_estimate", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
                 ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
-                ("seconds_filter_f32", ctypes.c_double)]
+                ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -18,6 +19,7 @@ namespace pfe {
 // Number of kernels this library has launched (all of its own kernels; cuBLAS/cuSOLVER excluded).
 int64_t launch_count();
 void count_launch();
+void count_launches(int64_t n);  // launches replayed inside a CUDA graph
 // Prefix of every kernel launch statement in this library: counts it, then launches.
 #define PFE_LAUNCH ::pfe::count_launch(),
 
@@ -102,6 +104,36 @@ void launch_rowmajor_to_colmajor(int64_t n, int32_t k, const T *R, int64_t ldr, 
 template <typename T>
 void launch_zero(T *p, int64_t count, cudaStream_t s);
 
+// Batched filter: one persistent launch per Chebyshev step over every sample's work items.
+// One descriptor per sample (device-resident, refreshed before every graph replay).
+struct BatchDesc {
+  const int32_t *rp;
+  const int32_t *ci;
+  const double *vals;  // filter operator A = (2/d)(H - cI)
+  const double *X;
+  double *b0, *b1, *Y;
+  const double *coef;  // m + 1 damped coefficients
+  int64_t ld;
+  int64_t item_begin;  // prefix of items over samples
+  int32_t n_atoms, k, m, nchunk;
+};
+void launch_batch_step(int cpl, int blocks, const BatchDesc *desc, int32_t nsamp, const int64_t *total, int32_t step,
+                       cudaStream_t s);
+
+// --------------------------------------------------------------------------------------
+// FP64 tensor-core (DMMA) products
+// --------------------------------------------------------------------------------------
+// C (m x nn, column-major ldc) = alpha A^T B + beta C for tall row-major A (K x m), B (K x nn);
+// with sym (A == B, m == nn) only the upper tile triangle is computed and mirrored.
+// work >= gram_work(K, m, nn, sym) doubles.
+int32_t gram_splits(int64_t K, int32_t m, int32_t nn, bool sym);
+size_t gram_work(int64_t K, int32_t m, int32_t nn, bool sym);
+void launch_gram(int64_t K, int32_t m, int32_t nn, const double *A, int64_t lda, const double *B, int64_t ldb,
+                 double alpha, double beta, double *C, int64_t ldc, bool sym, double *work, cudaStream_t s);
+// C (M x N row-major, ldc) = alpha A (M x K row-major, lda) Bc (K x N column-major, ldb) + beta C
+void launch_update(int64_t M, int32_t N, int32_t K, const double *A, int64_t lda, const double *Bc, int64_t ldb,
+                   double alpha, double beta, double *C, int64_t ldc, cudaStream_t s);
+
 // --------------------------------------------------------------------------------------
 // Host math of the filter (App. A, Sec. 2.3, eq. (thresh)); independent of the oracle
 // --------------------------------------------------------------------------------------
@@ -119,6 +151,24 @@ int32_t choose_degree(double xi, double eta, double eps, double r, int kind, int
 void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &beta, double *theta, double *last);
 
 }  // namespace pfe
+
+// --------------------------------------------------------------------------------------
+// State of one filtered subspace iteration (kept in the context between stages)
+// --------------------------------------------------------------------------------------
+struct SolveState {
+  bool fp32 = false, use64 = true, was64 = true, done = false, timed_filter = true;
+  int32_t q = 0, act = 0, nl = 0, it = 0, prev_count = -1, fp64_sweeps = 0;
+  int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
+  double t_start = 0, t_filter = 0, t_filter32 = 0, t_orth = 0, t_rr = 0, prev_worst = 1e300, window_est = -1.0;
+  pfe_status result = PFE_E_NOCONV;
+  double *X = nullptr, *Y = nullptr, *W = nullptr, *T0 = nullptr, *T1 = nullptr, *L = nullptr;
+  double *A = nullptr, *evals = nullptr, *red = nullptr, *resid2 = nullptr;
+  int32_t *idx = nullptr;
+  int *info = nullptr;
+  float *X32 = nullptr, *Y32 = nullptr, *B32a = nullptr, *B32b = nullptr;
+  std::vector<double> lockLam, lockRes, hth, hr2;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
 
 // --------------------------------------------------------------------------------------
 // The context
@@ -176,7 +226,11 @@ struct pfe_ctx {
 
   // workspaces
   pfe::DBuf w_X, w_Y, w_W, w_T0, w_T1, w_T2, w_small, w_small2, w_red, w_idx, w_cs_work, w_info, w_f32a, w_f32b,
-      w_f32c, w_f32d, w_ckpt, w_rr;
+      w_f32c, w_f32d, w_ckpt, w_rr, w_gram;
+  int64_t launch_base = 0;  // process-wide launch counter when the context was created
+  SolveState solve;
+  pfe::DBuf dcoef;            // filter coefficients on the device (batched solves)
+  int tuned_cpl = 0, tuned_blocks = 0;  // autotuned batched-filter shape of the last batch
   std::string err;
 };
 

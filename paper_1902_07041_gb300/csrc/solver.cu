@@ -265,67 +265,509 @@ pfe_status window_estimate(pfe_ctx *ctx, double *out) {
 }
 
 // ---------------------------------------------------------------- CholQR2 (+ shifted retry)
-// Y (row-major n x k, row stride ld) <- Y R^{-1} with R^T R = Y^T Y; repeated passes.
-pfe_status cholqr(pfe_ctx *ctx, double *Y, int32_t k, int64_t ld, bool *broke) {
+// One CholeskyQR pass: G = Y^T Y (DMMA Gram), R^T R = G (cuSOLVER potrf on the k x k matrix),
+// Out = Y R^{-1} (R^{-1} by a k x k triangular solve, then a DMMA block update).
+pfe_status cholqr(pfe_ctx *ctx, const double *Y, double *Out, int32_t k, int64_t ld, bool *broke) {
   const int64_t n = ctx->n;
-  RESERVE(double, G, ctx->w_small, (size_t)k * k);
+  cudaStream_t s = ctx->stream;
+  RESERVE(double, G, ctx->w_small, (size_t)2 * k * k);
+  double *Rinv = G + (size_t)k * k;
   RESERVE(int, info, ctx->w_info, 4);
+  RESERVE(double, gw, ctx->w_gram, gram_work(n, k, k, true));
   int lwork = 0;
   PFE_SOLVER_TRY(ctx, cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, &lwork));
   RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lwork, 1));
-  const double one = 1.0, zero = 0.0;
-  // G = Y^T Y: in column-major terms Y is Yc (k x n, ld) and G = Yc Yc^T
-  PFE_BLAS_TRY(ctx, cublasDsyrk(ctx->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, Y, (int)ld, &zero, G, k));
+  launch_gram(n, k, k, Y, ld, Y, ld, 1.0, 0.0, G, k, true, gw, s);
+  PFE_TRY(check_launch(ctx, "Gram"));
   PFE_SOLVER_TRY(ctx, cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, work, lwork, info));
   int hinfo = 0;
-  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   *broke = false;
   if (hinfo != 0) {
-    // shifted CholeskyQR (Fukaya et al. 2020): G + s I with s = 11 (n k + k (k + 1)) u ||Y||^2
+    // shifted CholeskyQR (Fukaya et al. 2020): G + s I with s = 11 (n k + k (k + 1)) u trace(G)
     *broke = true;
-    PFE_BLAS_TRY(ctx, cublasDsyrk(ctx->blas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, k, (int)n, &one, Y, (int)ld, &zero, G, k));
+    launch_gram(n, k, k, Y, ld, Y, ld, 1.0, 0.0, G, k, true, gw, s);
     std::vector<double> hG((size_t)k * k);
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, ctx->stream));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     double tr = 0.0;
     for (int32_t i = 0; i < k; ++i) tr += hG[(size_t)i * k + i];
     const double sh = 11.0 * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
     for (int32_t i = 0; i < k; ++i) hG[(size_t)i * k + i] += sh;
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(G, hG.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(G, hG.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
     PFE_SOLVER_TRY(ctx, cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, work, lwork, info));
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hinfo != 0) return pfe_fail(ctx, PFE_E_BREAKDOWN, "CholeskyQR broke down even with a shift");
   }
-  // Y R^{-1}: Yc <- R^{-T} Yc
-  PFE_BLAS_TRY(ctx, cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T, CUBLAS_DIAG_NON_UNIT, k,
-                                (int)n, &one, G, k, Y, (int)ld));
-  return PFE_OK;
+  // R^{-1}: solve R Z = I (k x k, upper triangular)
+  {
+    std::vector<double> eye((size_t)k * k, 0.0);
+    for (int32_t i = 0; i < k; ++i) eye[(size_t)i * k + i] = 1.0;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(Rinv, eye.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
+    const double one = 1.0;
+    PFE_BLAS_TRY(ctx, cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                                  CUBLAS_DIAG_NON_UNIT, k, k, &one, G, k, Rinv, k));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // eye must outlive its copy
+  }
+  launch_update(n, k, k, Y, ld, Rinv, k, 1.0, 0.0, Out, ld, s);
+  return check_launch(ctx, "CholeskyQR update");
 }
 
-pfe_status cholqr2(pfe_ctx *ctx, double *Y, int32_t k, int64_t ld) {
+// CholQR2 of Y using tmp as the second buffer; *result points to the buffer holding Q.
+pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result) {
+  *result = Y;
   if (k <= 0) return PFE_OK;
   bool broke = false;
-  PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
-  PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
-  if (broke) PFE_TRY(cholqr(ctx, Y, k, ld, &broke));
+  PFE_TRY(cholqr(ctx, Y, tmp, k, ld, &broke));
+  PFE_TRY(cholqr(ctx, tmp, Y, k, ld, &broke));
+  if (broke) {
+    PFE_TRY(cholqr(ctx, Y, tmp, k, ld, &broke));
+    *result = tmp;
+  }
   return PFE_OK;
 }
 
-// Y <- Y - L (L^T Y), twice (classical Gram-Schmidt against the locked block)
+// Y <- Y - L (L^T Y), twice (classical Gram-Schmidt against the locked block), DMMA products
 pfe_status project_out(pfe_ctx *ctx, const double *L, int32_t nl, double *Y, int32_t k, int64_t ld) {
   if (nl <= 0 || k <= 0) return PFE_OK;
   const int64_t n = ctx->n;
   RESERVE(double, h, ctx->w_small2, (size_t)nl * k);
-  const double one = 1.0, zero = 0.0, mone = -1.0;
+  RESERVE(double, gw, ctx->w_gram, gram_work(n, nl, k, false));
   for (int pass = 0; pass < 2; ++pass) {
-    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, nl, k, (int)n, &one, L, (int)ld, Y, (int)ld,
-                                  &zero, h, nl));
-    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, k, (int)n, nl, &mone, h, nl, L, (int)ld, &one, Y,
-                                  (int)ld));
+    launch_gram(n, nl, k, L, ld, Y, ld, 1.0, 0.0, h, nl, false, gw, ctx->stream);
+    launch_update(n, k, nl, L, ld, h, nl, -1.0, 1.0, Y, ld, ctx->stream);
+  }
+  return check_launch(ctx, "projection");
+}
+
+// ---------------------------------------------------------------- the solve, in stages
+// solve_setup: filter design, width, buffers, random start block.  solve_filter: Y = p(Ht) X
+// on the active columns.  solve_after_filter: project out the locked block, CholQR2,
+// Rayleigh-Ritz, residuals, locking and the termination test.  solve_finish: results.
+// pfe_solve runs them for one context; pfe_solve_batch interleaves many contexts and replaces
+// solve_filter by one batched persistent launch per Chebyshev step.
+pfe_status solve_setup(pfe_ctx *ctx) {
+  SolveState &st = ctx->solve;
+  for (int e = 0; e < 4; ++e)
+    if (st.ev[e]) cudaEventDestroy(st.ev[e]);
+  st = SolveState{};
+  if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
+  st.t_start = now_s();
+  ctx->has_result = false;
+  ctx->n_found = 0;
+  ctx->stats = pfe_stats{};
+  st.fp32 = ctx->p_precision == 1;
+  PFE_TRY(ensure_filter(ctx));
+  PFE_TRY(ensure_hs(ctx, st.fp32));
+  int32_t q = ctx->p_width;
+  if (q <= 0) {
+    PFE_TRY(count_estimate(ctx));
+    PFE_TRY(window_estimate(ctx, &st.window_est));
+    const double qa = ctx->p_width_factor * std::max(ctx->count_est, 0.0);
+    const double qw = 1.1 * std::max(st.window_est, 0.0) + 8.0;
+    q = (int32_t)std::ceil(std::max(qa, qw));
+    q = std::max(q, ctx->p_min_width);
+  }
+  q = (int32_t)std::min<int64_t>(q, ctx->n);
+  const int64_t n = ctx->n, ld = round_up(q, 4);
+  st.q = q;
+  st.ld = ld;
+  ctx->ldq = ld;
+  cudaStream_t s = ctx->stream;
+  const size_t big = (size_t)n * ld;
+  RESERVE(double, X, ctx->w_X, big);
+  RESERVE(double, Y, ctx->w_Y, big);
+  RESERVE(double, W, ctx->w_W, big);
+  RESERVE(double, T0, ctx->w_T0, big);
+  RESERVE(double, T1, ctx->w_T1, big);
+  RESERVE(double, L, ctx->L, big);
+  RESERVE(double, A, ctx->w_rr, (size_t)q * q + (size_t)q + 8);
+  RESERVE(double, red, ctx->w_red, colreduce_work(n, q) + (size_t)q + 8);
+  RESERVE(int32_t, idx, ctx->w_idx, (size_t)q + 8);
+  RESERVE(int, info, ctx->w_info, 4);
+  st.X = X; st.Y = Y; st.W = W; st.T0 = T0; st.T1 = T1; st.L = L;
+  st.A = A;
+  st.evals = A + (size_t)q * q;
+  st.red = red;
+  st.resid2 = red + colreduce_work(n, q);
+  st.idx = idx;
+  st.info = info;
+  if (st.fp32) {
+    RESERVE(float, x32, ctx->w_f32a, big);
+    RESERVE(float, y32, ctx->w_f32b, big);
+    RESERVE(float, a32, ctx->w_f32c, big);
+    RESERVE(float, b32, ctx->w_f32d, big);
+    st.X32 = x32; st.Y32 = y32; st.B32a = a32; st.B32b = b32;
+    for (float *p : {x32, y32, a32, b32}) launch_zero<float>(p, (int64_t)big, s);
+  }
+  for (double *p : {X, Y, W, T0, T1, L}) launch_zero<double>(p, (int64_t)big, s);
+  for (int e = 0; e < 4; ++e)
+    if (!st.ev[e]) PFE_CUDA_TRY(ctx, cudaEventCreate(&st.ev[e]));
+  // start block (stream 0 of the seeded Philox normals) and its orthonormalisation
+  launch_fill_normal<double>(ctx->p_seed, 0u, n, q, 0, st.X, ld, s);
+  PFE_TRY(check_launch(ctx, "start block"));
+  {
+    double *res = nullptr;
+    PFE_TRY(cholqr2(ctx, st.X, st.T0, q, ld, &res));
+    if (res != st.X) std::swap(st.X, st.T0);
+  }
+  st.act = q;
+  st.use64 = !st.fp32;
+  st.hth.resize(q);
+  st.hr2.resize(q);
+  st.it = 0;
+  return PFE_OK;
+}
+
+// Y = p(Ht) X on the active columns (the single-context path)
+pfe_status solve_filter(pfe_ctx *ctx) {
+  SolveState &st = ctx->solve;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n, ld = st.ld;
+  st.was64 = st.use64;
+  st.f_launch += std::max(ctx->m, 1);
+  (st.use64 ? st.f_cols64 : st.f_cols32) += (int64_t)st.act * std::max(ctx->m, 1);
+  if (st.use64) {
+    PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, st.act, ld, st.X, st.Y, st.T0, st.T1, s));
+    ++st.fp64_sweeps;
+  } else {
+    launch_convert<double, float>(n, st.act, st.X, ld, st.X32, ld, s);
+    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, st.act, ld, st.X32, st.Y32, st.B32a,
+                              st.B32b, s));
+    launch_convert<float, double>(n, st.act, st.Y32, ld, st.Y, ld, s);
+  }
+  st.matvecs += (int64_t)st.act * ctx->m;
+  return PFE_OK;
+}
+
+// Everything of one iteration after the filter; sets st.done when the solve has ended.
+pfe_status solve_after_filter(pfe_ctx *ctx) {
+  SolveState &st = ctx->solve;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n, ld = st.ld;
+  const int32_t q = st.q;
+  ++st.it;
+  const int32_t act = st.act;
+  cudaEventRecord(st.ev[1], s);
+  // ---- orthonormalise against the locked vectors and within the block
+  PFE_TRY(project_out(ctx, st.L, st.nl, st.Y, act, ld));
+  {
+    double *res = nullptr;
+    PFE_TRY(cholqr2(ctx, st.Y, st.T0, act, ld, &res));
+    if (res != st.Y) std::swap(st.Y, st.T0);
+  }
+  std::swap(st.X, st.Y);
+  cudaEventRecord(st.ev[2], s);
+  // ---- Rayleigh-Ritz with H: W = H X, A = X^T W, A = Q Theta Q^T, X <- X Q, W <- W Q
+  launch_bsr_step<double>(bsr_H(ctx), MODE_SPMM, act, ld, st.X, nullptr, st.W, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+  PFE_TRY(check_launch(ctx, "H X"));
+  st.matvecs += act;
+  {
+    RESERVE(double, gw, ctx->w_gram, gram_work(n, act, act, false));
+    launch_gram(n, act, act, st.X, ld, st.W, ld, 1.0, 0.0, st.A, act, false, gw, s);
+  }
+  int lw = 0;
+  PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act,
+                                                  st.A, act, st.resid2, &lw));
+  RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
+  PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, st.A, act,
+                                       st.evals, work, lw, st.info));
+  launch_update(n, act, act, st.X, ld, st.A, act, 1.0, 0.0, st.Y, ld, s);
+  std::swap(st.X, st.Y);
+  launch_update(n, act, act, st.W, ld, st.A, act, 1.0, 0.0, st.T0, ld, s);
+  std::swap(st.W, st.T0);
+  launch_col_resid2(n, act, st.W, st.X, ld, st.evals, st.resid2, st.red, s);
+  PFE_TRY(check_launch(ctx, "residuals"));
+  cudaEventRecord(st.ev[3], s);
+  int hinfo = 0;
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.hth.data(), st.evals, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.hr2.data(), st.resid2, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, st.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge (info " + std::to_string(hinfo) + ")");
+  float ms = 0;
+  if (st.timed_filter) {
+    cudaEventElapsedTime(&ms, st.ev[0], st.ev[1]);
+    st.t_filter += ms * 1e-3;
+    if (!st.was64) st.t_filter32 += ms * 1e-3;
+  }
+  cudaEventElapsedTime(&ms, st.ev[1], st.ev[2]);
+  st.t_orth += ms * 1e-3;
+  cudaEventElapsedTime(&ms, st.ev[2], st.ev[3]);
+  st.t_rr += ms * 1e-3;
+  const double lmax = ctx->lmax, tol = ctx->p_tol;
+
+  // ---- convergence bookkeeping.  Converged: r <= tol.  An unconverged pair blocks termination
+  // only when its residual interval [theta - r, theta + r] lies inside [a, b]: the Krylov-Weinstein
+  // bound then places a not yet locked eigenvalue in the interval.  Other unconverged Ritz values
+  // in [a, b] can be mixtures of eigenvectors from both sides and never converge.
+  std::vector<double> rr(act);
+  double worst_inside = 0.0;
+  int count_in = 0, unconv_in = 0;
+  for (double lv : st.lockLam)
+    if (lv >= ctx->a && lv <= ctx->b) ++count_in;
+  for (int32_t j = 0; j < act; ++j) {
+    rr[j] = std::sqrt(std::max(st.hr2[j], 0.0)) / lmax;
+    if (!std::isfinite(st.hth[j]) || !std::isfinite(rr[j]))
+      return pfe_fail(ctx, PFE_E_BREAKDOWN, "non-finite Ritz value or residual");
+    if (st.hth[j] > lmax * (1.0 + 1e-12)) return pfe_fail(ctx, PFE_E_BOUND, "a Ritz value exceeds the lambda_max bound");
+    const double rabs = rr[j] * lmax;
+    if (st.hth[j] >= ctx->a && st.hth[j] <= ctx->b && rr[j] > tol) worst_inside = std::max(worst_inside, rr[j]);
+    if (rr[j] <= tol) {
+      if (st.hth[j] >= ctx->a && st.hth[j] <= ctx->b) ++count_in;
+    } else if (st.hth[j] - rabs >= ctx->a && st.hth[j] + rabs <= ctx->b) {
+      ++unconv_in;
+    }
+  }
+  // ---- lock converged pairs and compact the active block
+  std::vector<int32_t> lock_cols, keep_cols;
+  for (int32_t j = 0; j < act; ++j) {
+    if (rr[j] <= tol && st.nl + (int32_t)lock_cols.size() < q) lock_cols.push_back(j);
+    else keep_cols.push_back(j);
+  }
+  if (!lock_cols.empty()) {
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, lock_cols.data(), sizeof(int32_t) * lock_cols.size(),
+                                      cudaMemcpyHostToDevice, s));
+    launch_gather_cols(n, (int32_t)lock_cols.size(), st.X, ld, st.L + st.nl, ld, st.idx, s);
+    for (int32_t j : lock_cols) {
+      st.lockLam.push_back(st.hth[j]);
+      st.lockRes.push_back(rr[j]);
+    }
+    st.nl += (int32_t)lock_cols.size();
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, keep_cols.data(), sizeof(int32_t) * std::max<size_t>(keep_cols.size(), 1),
+                                      cudaMemcpyHostToDevice, s));
+    launch_gather_cols(n, (int32_t)keep_cols.size(), st.X, ld, st.Y, ld, st.idx, s);
+    std::swap(st.X, st.Y);
+    PFE_TRY(check_launch(ctx, "locking"));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the host index vectors must outlive the copies
+  }
+  st.act = (int32_t)keep_cols.size();
+  // FP32 filter: hand over to FP64 sweeps once the unconverged interval pairs are below the
+  // refinement tolerance or stop improving (the FP32 subspace has reached its accuracy floor)
+  if (!st.use64 && st.it >= 2 && (worst_inside < ctx->p_refine_tol || worst_inside > 0.5 * st.prev_worst))
+    st.use64 = true;
+  st.prev_worst = worst_inside;
+  if ((unconv_in == 0 && count_in == st.prev_count && st.it >= 2) || st.act == 0) {
+    st.result = (count_in >= q) ? PFE_E_CAPACITY : PFE_OK;
+    st.done = true;
+  } else if (st.it >= ctx->p_max_iters) {
+    st.result = PFE_E_NOCONV;
+    st.done = true;
+  }
+  st.prev_count = count_in;
+  return PFE_OK;
+}
+
+pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
+  SolveState &st = ctx->solve;
+  const double lmax = ctx->lmax;
+  std::vector<int32_t> ord;
+  for (int32_t l = 0; l < st.nl; ++l)
+    if (st.lockLam[l] >= ctx->a && st.lockLam[l] <= ctx->b) ord.push_back(l);
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return st.lockLam[x] < st.lockLam[y]; });
+  ctx->result_cols = ord;
+  ctx->result_lam.clear();
+  ctx->result_res.clear();
+  double maxres = 0.0;
+  for (int32_t l : ord) {
+    ctx->result_lam.push_back(st.lockLam[l]);
+    ctx->result_res.push_back(st.lockRes[l] * lmax);
+    maxres = std::max(maxres, st.lockRes[l]);
+  }
+  ctx->n_found = (int32_t)ord.size();
+  ctx->has_result = true;
+  pfe_stats &o = ctx->stats;
+  o.iterations = st.it;
+  o.width = st.q;
+  o.degree = ctx->m;
+  o.n_found = ctx->n_found;
+  o.matvecs = st.matvecs;
+  o.lambda_max = lmax;
+  o.count_estimate = ctx->has_count ? ctx->count_est : -1.0;
+  o.window_estimate = st.window_est;
+  o.seconds_filter = st.t_filter;
+  o.seconds_filter_f32 = st.t_filter32;
+  o.seconds_orth = st.t_orth;
+  o.seconds_rr = st.t_rr;
+  o.max_residual = maxres;
+  o.fp64_sweeps = st.fp64_sweeps;
+  o.status = (int32_t)st.result;
+  o.kernel_launches = launch_count() - ctx->launch_base;
+  o.filter_launches = st.f_launch;
+  o.filter_col_steps = st.f_cols64;
+  o.filter_col_steps_f32 = st.f_cols32;
+  o.seconds_total = now_s() - st.t_start;
+  for (int e = 0; e < 4; ++e)
+    if (st.ev[e]) {
+      cudaEventDestroy(st.ev[e]);
+      st.ev[e] = nullptr;
+    }
+  if (n_found) *n_found = ctx->n_found;
+  if (st.result == PFE_E_CAPACITY) return pfe_fail(ctx, st.result, "every Ritz vector lies in [a, b]: raise PFE_P_WIDTH");
+  if (st.result == PFE_E_NOCONV) return pfe_fail(ctx, st.result, "iteration limit reached");
+  return PFE_OK;
+}
+
+// ---------------------------------------------------------------- batched filter (host side)
+struct BatchPlan {
+  DBuf desc, total;
+  std::vector<BatchDesc> h;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t m_max = 0, cpl = 2, blocks = 0;
+  cudaStream_t stream = nullptr;  // the batch's own stream (graphs cannot be captured on the legacy stream)
+  cudaEvent_t e0 = nullptr, e1 = nullptr, done_ev = nullptr;
+};
+
+void batch_plan_free(BatchPlan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->e0) cudaEventDestroy(p->e0);
+  if (p->e1) cudaEventDestroy(p->e1);
+  if (p->done_ev) cudaEventDestroy(p->done_ev);
+  if (p->stream) {
+    cudaStreamSynchronize(p->stream);
+    cudaStreamDestroy(p->stream);
+  }
+  dbuf_free(p->desc);
+  dbuf_free(p->total);
+  *p = BatchPlan{};
+}
+
+// Refresh the descriptors of the FP64 samples that are still iterating; returns the item count.
+int64_t batch_refresh(pfe_ctx **ctxs, int32_t ns, const std::vector<pfe_status> &status, BatchPlan *p) {
+  int64_t items = 0;
+  p->h.resize(ns);
+  for (int32_t i = 0; i < ns; ++i) {
+    pfe_ctx *c = ctxs[i];
+    const SolveState &st = c->solve;
+    BatchDesc &d = p->h[i];
+    const bool live = status[i] == PFE_OK && !st.done && st.use64;
+    d.rp = c->rp.as<int32_t>();
+    d.ci = c->ci.as<int32_t>();
+    d.vals = c->Hs64.as<double>();
+    d.X = st.X;
+    d.b0 = st.T0;
+    d.b1 = st.T1;
+    d.Y = st.Y;
+    d.coef = c->dcoef.as<double>();
+    d.ld = st.ld;
+    d.n_atoms = c->N;
+    d.k = live ? st.act : 0;
+    d.m = live ? c->m : 0;
+    d.nchunk = (d.k + 32 * p->cpl - 1) / (32 * p->cpl);
+    d.item_begin = items;
+    items += (int64_t)d.n_atoms * d.nchunk;
+  }
+  return items;
+}
+
+pfe_status batch_upload(pfe_ctx *c0, BatchPlan *p, int64_t items) {
+  cudaStream_t s = p->stream;
+  PFE_CUDA_TRY(c0, cudaMemcpyAsync(p->desc.p, p->h.data(), sizeof(BatchDesc) * p->h.size(), cudaMemcpyHostToDevice, s));
+  PFE_CUDA_TRY(c0, cudaMemcpyAsync(p->total.p, &items, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PFE_CUDA_TRY(c0, cudaStreamSynchronize(s));  // the host copies must outlive the transfers
+  return PFE_OK;
+}
+
+pfe_status batch_plan_init(pfe_ctx *c0, pfe_ctx **ctxs, int32_t ns, const std::vector<pfe_status> &status,
+                           BatchPlan *p) {
+  PFE_CUDA_TRY(c0, cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+  cudaStream_t s = p->stream;
+  for (int32_t i = 0; i < ns; ++i) {
+    if (status[i] != PFE_OK) continue;
+    pfe_ctx *c = ctxs[i];
+    // coefficients on the device (read by the batched kernel)
+    if (dbuf_reserve(c->dcoef, sizeof(double) * (c->m + 1)) != cudaSuccess)
+      return pfe_fail(c0, PFE_E_NOMEM, "coefficient buffer");
+    PFE_CUDA_TRY(c0, cudaMemcpy(c->dcoef.p, c->coef.data(), sizeof(double) * (c->m + 1), cudaMemcpyHostToDevice));
+    p->m_max = std::max(p->m_max, c->m);
+    PFE_CUDA_TRY(c0, cudaStreamSynchronize(c->stream));  // set-up work of every sample is complete
+  }
+  if (dbuf_reserve(p->desc, sizeof(BatchDesc) * ns) != cudaSuccess || dbuf_reserve(p->total, sizeof(int64_t)) != cudaSuccess)
+    return pfe_fail(c0, PFE_E_NOMEM, "batch descriptors");
+  PFE_CUDA_TRY(c0, cudaEventCreate(&p->e0));
+  PFE_CUDA_TRY(c0, cudaEventCreate(&p->e1));
+  PFE_CUDA_TRY(c0, cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming));
+  int sms = 0;
+  PFE_CUDA_TRY(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+  // autotuner: columns per warp (32 or 64) x persistent blocks per SM, timed on steps 0 and 1
+  // (they write only scratch buffers), best of two trials each
+  float best = 1e30f;
+  int best_cpl = 2, best_blocks = sms * 8;
+  if (p->m_max >= 2) {
+    for (int cpl : {1, 2})
+      for (int bps : {4, 8, 16}) {
+        p->cpl = cpl;
+        const int64_t items = batch_refresh(ctxs, ns, status, p);
+        if (items == 0) continue;
+        PFE_TRY(batch_upload(c0, p, items));
+        float t_best = 1e30f;
+        for (int trial = 0; trial < 2; ++trial) {
+          cudaEventRecord(p->e0, s);
+          launch_batch_step(cpl, sms * bps, p->desc.as<BatchDesc>(), ns, p->total.as<int64_t>(), 0, s);
+          launch_batch_step(cpl, sms * bps, p->desc.as<BatchDesc>(), ns, p->total.as<int64_t>(), 1, s);
+          cudaEventRecord(p->e1, s);
+          PFE_CUDA_TRY(c0, cudaEventSynchronize(p->e1));
+          float ms = 0;
+          cudaEventElapsedTime(&ms, p->e0, p->e1);
+          t_best = std::min(t_best, ms);
+        }
+        PFE_TRY(check_launch(c0, "batch autotune"));
+        if (t_best < best) {
+          best = t_best;
+          best_cpl = cpl;
+          best_blocks = sms * bps;
+        }
+      }
+  }
+  p->cpl = best_cpl;
+  p->blocks = best_blocks;
+  c0->tuned_cpl = best_cpl;
+  c0->tuned_blocks = best_blocks;
+  // capture the m_max steps of one filter application as a CUDA graph
+  if (p->m_max > 0) {
+    PFE_CUDA_TRY(c0, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int32_t j = 0; j < p->m_max; ++j)
+      launch_batch_step(p->cpl, p->blocks, p->desc.as<BatchDesc>(), ns, p->total.as<int64_t>(), j, s);
+    cudaError_t ce = cudaStreamEndCapture(s, &p->graph);
+    if (ce != cudaSuccess) return pfe_fail(c0, PFE_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    PFE_CUDA_TRY(c0, cudaGraphInstantiate(&p->exec, p->graph, 0));
   }
   return PFE_OK;
+}
+
+// One filter application for every FP64 sample: refresh descriptors, replay the graph.
+pfe_status batch_filter(pfe_ctx *c0, pfe_ctx **ctxs, int32_t ns, const std::vector<pfe_status> &status, BatchPlan *p,
+                        float *ms) {
+  cudaStream_t s = p->stream;
+  *ms = 0.f;
+  const int64_t items = batch_refresh(ctxs, ns, status, p);
+  for (int32_t i = 0; i < ns; ++i) {
+    const BatchDesc &d = p->h[i];
+    if (d.k == 0) continue;
+    SolveState &st = ctxs[i]->solve;
+    st.was64 = true;
+    st.f_launch += std::max(d.m, 1);
+    st.f_cols64 += (int64_t)d.k * std::max(d.m, 1);
+    st.matvecs += (int64_t)d.k * d.m;
+    ++st.fp64_sweeps;
+    // degree 0: y = g0 x (no Chebyshev step)
+    if (d.m == 0) launch_axpby<double>(ctxs[i]->n, d.k, ctxs[i]->coef[0], st.X, st.ld, 0.0, st.Y, st.ld, ctxs[i]->stream);
+  }
+  if (items > 0 && p->exec) {
+    PFE_TRY(batch_upload(c0, p, items));
+    cudaEventRecord(p->e0, s);
+    PFE_CUDA_TRY(c0, cudaGraphLaunch(p->exec, s));
+    cudaEventRecord(p->e1, s);
+    PFE_CUDA_TRY(c0, cudaEventSynchronize(p->e1));
+    cudaEventElapsedTime(ms, p->e0, p->e1);
+    count_launches(p->m_max);
+  }
+  cudaEventRecord(p->done_ev, s);
+  return check_launch(c0, "batched filter");
 }
 
 }  // namespace
@@ -470,6 +912,7 @@ pfe_status pfe_create(pfe_ctx **out, int32_t n_atoms, int64_t nnzb, const int32_
   if (!ctx) return PFE_E_NOMEM;
   ctx->N = n_atoms;
   ctx->n = 3 * (int64_t)n_atoms;
+  ctx->launch_base = launch_count();
   ctx->nnzb = nnzb;
   ctx->has_mass = masses != nullptr;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -515,8 +958,10 @@ void pfe_destroy(pfe_ctx *ctx) {
   DBuf *bufs[] = {&ctx->rp, &ctx->ci, &ctx->H, &ctx->mass, &ctx->Hs64, &ctx->Hs32, &ctx->L, &ctx->w_X, &ctx->w_Y,
                   &ctx->w_W, &ctx->w_T0, &ctx->w_T1, &ctx->w_T2, &ctx->w_small, &ctx->w_small2, &ctx->w_red,
                   &ctx->w_idx, &ctx->w_cs_work, &ctx->w_info, &ctx->w_f32a, &ctx->w_f32b, &ctx->w_f32c,
-                  &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr};
+                  &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram};
   for (DBuf *b : bufs) dbuf_free(*b);
+  for (int e = 0; e < 4; ++e)
+    if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
   if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   delete ctx;
@@ -686,237 +1131,15 @@ pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs,
 
 pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
   if (!ctx) return PFE_E_ARG;
-  if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
   if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
-  const double t_start = now_s();
-  ctx->has_result = false;
-  ctx->n_found = 0;
-  ctx->stats = pfe_stats{};
-  const bool fp32 = ctx->p_precision == 1;
-  PFE_TRY(ensure_filter(ctx));
-  PFE_TRY(ensure_hs(ctx, fp32));
-  int32_t q = ctx->p_width;
-  double window_est = -1.0;
-  if (q <= 0) {
-    PFE_TRY(count_estimate(ctx));
-    PFE_TRY(window_estimate(ctx, &window_est));
-    const double qa = ctx->p_width_factor * std::max(ctx->count_est, 0.0);
-    const double qw = 1.1 * std::max(window_est, 0.0) + 8.0;
-    q = (int32_t)std::ceil(std::max(qa, qw));
-    q = std::max(q, ctx->p_min_width);
+  SolveState &st = ctx->solve;
+  PFE_TRY(solve_setup(ctx));
+  while (!st.done) {
+    cudaEventRecord(st.ev[0], ctx->stream);
+    PFE_TRY(solve_filter(ctx));
+    PFE_TRY(solve_after_filter(ctx));
   }
-  q = (int32_t)std::min<int64_t>(q, ctx->n);
-  const int64_t n = ctx->n, ld = round_up(q, 4);
-  ctx->ldq = ld;
-  cudaStream_t s = ctx->stream;
-  const size_t big = (size_t)n * ld;
-  RESERVE(double, X, ctx->w_X, big);
-  RESERVE(double, Y, ctx->w_Y, big);
-  RESERVE(double, W, ctx->w_W, big);
-  RESERVE(double, T0, ctx->w_T0, big);
-  RESERVE(double, T1, ctx->w_T1, big);
-  RESERVE(double, L, ctx->L, big);
-  RESERVE(double, A, ctx->w_rr, (size_t)q * q + (size_t)q + 8);
-  double *evals = A + (size_t)q * q;  // Ritz values from the dense eigensolver
-  RESERVE(double, red, ctx->w_red, colreduce_work(n, q) + (size_t)q + 8);
-  double *resid2 = red + colreduce_work(n, q);
-  RESERVE(int32_t, idx, ctx->w_idx, (size_t)q + 8);
-  RESERVE(int, info, ctx->w_info, 4);
-  float *X32 = nullptr, *Y32 = nullptr, *B32a = nullptr, *B32b = nullptr;
-  if (fp32) {
-    RESERVE(float, x32, ctx->w_f32a, big);
-    RESERVE(float, y32, ctx->w_f32b, big);
-    RESERVE(float, a32, ctx->w_f32c, big);
-    RESERVE(float, b32, ctx->w_f32d, big);
-    X32 = x32; Y32 = y32; B32a = a32; B32b = b32;
-    for (float *p : {X32, Y32, B32a, B32b}) launch_zero<float>(p, (int64_t)big, s);
-  }
-  for (double *p : {X, Y, W, T0, T1, L}) launch_zero<double>(p, (int64_t)big, s);
-
-  cudaEvent_t ev0, ev1, ev2, ev3;
-  cudaEventCreate(&ev0);
-  cudaEventCreate(&ev1);
-  cudaEventCreate(&ev2);
-  cudaEventCreate(&ev3);
-  struct EvGuard {
-    cudaEvent_t *e;
-    ~EvGuard() {
-      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
-    }
-  };
-  cudaEvent_t evs[4] = {ev0, ev1, ev2, ev3};
-  EvGuard guard{evs};
-
-  // start block (stream 0 of the seeded Philox normals) and its orthonormalisation
-  launch_fill_normal<double>(ctx->p_seed, 0u, n, q, 0, X, ld, s);
-  PFE_TRY(check_launch(ctx, "start block"));
-  PFE_TRY(cholqr2(ctx, X, q, ld));
-
-  const double lmax = ctx->lmax, tol = ctx->p_tol;
-  int32_t act = q, nl = 0;
-  std::vector<double> lockLam, lockRes;
-  std::vector<double> hth(q), hr2(q);
-  int prev_count = -1, it = 0;
-  double prev_worst = 1e300;
-  pfe_status result = PFE_E_NOCONV;
-  bool use64 = !fp32;
-  int32_t fp64_sweeps = 0;
-  double t_filter = 0, t_filter32 = 0, t_orth = 0, t_rr = 0;
-  int64_t matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
-  const int64_t launches0 = launch_count();
-  for (it = 1; it <= ctx->p_max_iters; ++it) {
-    cudaEventRecord(ev0, s);
-    // ---- filter (Alg. 2) on the active columns
-    const bool was64 = use64;
-    f_launch += std::max(ctx->m, 1);
-    (use64 ? f_cols64 : f_cols32) += (int64_t)act * std::max(ctx->m, 1);
-    if (use64) {
-      PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, act, ld, X, Y, T0, T1, s));
-      ++fp64_sweeps;
-    } else {
-      launch_convert<double, float>(n, act, X, ld, X32, ld, s);
-      PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, act, ld, X32, Y32, B32a, B32b, s));
-      launch_convert<float, double>(n, act, Y32, ld, Y, ld, s);
-    }
-    matvecs += (int64_t)act * ctx->m;
-    cudaEventRecord(ev1, s);
-    // ---- orthonormalise against the locked vectors and within the block
-    PFE_TRY(project_out(ctx, L, nl, Y, act, ld));
-    PFE_TRY(cholqr2(ctx, Y, act, ld));
-    std::swap(X, Y);
-    cudaEventRecord(ev2, s);
-    // ---- Rayleigh-Ritz with H: W = H X, A = X^T W, A = Q Theta Q^T, X <- X Q, W <- W Q
-    launch_bsr_step<double>(bsr_H(ctx), MODE_SPMM, act, ld, X, nullptr, W, nullptr, 1.0, 0.0, 0.0, 0.0, s);
-    PFE_TRY(check_launch(ctx, "H X"));
-    matvecs += act;
-    const double one = 1.0, zero = 0.0;
-    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, act, act, (int)n, &one, X, (int)ld, W, (int)ld,
-                                  &zero, A, act));
-    int lw = 0;
-    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, A,
-                                                    act, resid2, &lw));
-    RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
-    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, A, act,
-                                         evals, work, lw, info));
-    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, act, (int)n, act, &one, A, act, X, (int)ld, &zero,
-                                  Y, (int)ld));
-    std::swap(X, Y);
-    PFE_BLAS_TRY(ctx, cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, act, (int)n, act, &one, A, act, W, (int)ld, &zero,
-                                  T0, (int)ld));
-    std::swap(W, T0);
-    launch_col_resid2(n, act, W, X, ld, evals, resid2, red, s);
-    PFE_TRY(check_launch(ctx, "residuals"));
-    cudaEventRecord(ev3, s);
-    int hinfo = 0;
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hth.data(), evals, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hr2.data(), resid2, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge (info " + std::to_string(hinfo) + ")");
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    t_filter += ms * 1e-3;
-    if (!was64) t_filter32 += ms * 1e-3;
-    cudaEventElapsedTime(&ms, ev1, ev2);
-    t_orth += ms * 1e-3;
-    cudaEventElapsedTime(&ms, ev2, ev3);
-    t_rr += ms * 1e-3;
-
-    // ---- convergence bookkeeping.  Converged: r <= tol.  An unconverged pair blocks termination
-    // only when its residual interval [theta - r, theta + r] lies inside [a, b]: the Krylov-Weinstein
-    // bound then places a not yet locked eigenvalue in the interval.  Other unconverged Ritz values
-    // in [a, b] can be mixtures of eigenvectors from both sides and never converge.
-    std::vector<double> rr(act);
-    double worst_unconv = 0.0;
-    int count_in = 0, unconv_in = 0;
-    for (double lv : lockLam)
-      if (lv >= ctx->a && lv <= ctx->b) ++count_in;
-    for (int32_t j = 0; j < act; ++j) {
-      rr[j] = std::sqrt(std::max(hr2[j], 0.0)) / lmax;
-      if (!std::isfinite(hth[j]) || !std::isfinite(rr[j]))
-        return pfe_fail(ctx, PFE_E_BREAKDOWN, "non-finite Ritz value or residual");
-      if (hth[j] > lmax * (1.0 + 1e-12)) return pfe_fail(ctx, PFE_E_BOUND, "a Ritz value exceeds the lambda_max bound");
-      const double rabs = rr[j] * lmax;
-      if (rr[j] <= tol) {
-        if (hth[j] >= ctx->a && hth[j] <= ctx->b) ++count_in;
-      } else if (hth[j] - rabs >= ctx->a && hth[j] + rabs <= ctx->b) {
-        ++unconv_in;
-        worst_unconv = std::max(worst_unconv, rr[j]);
-      }
-    }
-    // ---- lock converged pairs and compact the active block
-    std::vector<int32_t> lock_cols, keep_cols;
-    for (int32_t j = 0; j < act; ++j) {
-      if (rr[j] <= tol && nl + (int32_t)lock_cols.size() < q) lock_cols.push_back(j);
-      else keep_cols.push_back(j);
-    }
-    if (!lock_cols.empty()) {
-      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(idx, lock_cols.data(), sizeof(int32_t) * lock_cols.size(), cudaMemcpyHostToDevice, s));
-      launch_gather_cols(n, (int32_t)lock_cols.size(), X, ld, L + nl, ld, idx, s);
-      for (int32_t j : lock_cols) {
-        lockLam.push_back(hth[j]);
-        lockRes.push_back(rr[j]);
-      }
-      nl += (int32_t)lock_cols.size();
-      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(idx, keep_cols.data(), sizeof(int32_t) * std::max<size_t>(keep_cols.size(), 1),
-                                        cudaMemcpyHostToDevice, s));
-      launch_gather_cols(n, (int32_t)keep_cols.size(), X, ld, Y, ld, idx, s);
-      std::swap(X, Y);
-      PFE_TRY(check_launch(ctx, "locking"));
-      // the host vectors above must outlive the async copies
-      PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    }
-    act = (int32_t)keep_cols.size();
-    // FP32 filter: hand over to FP64 sweeps once the FP32 subspace stops improving
-    if (!use64 && (unconv_in == 0 || worst_unconv < ctx->p_refine_tol || worst_unconv > 0.5 * prev_worst)) use64 = true;
-    prev_worst = worst_unconv;
-    if ((unconv_in == 0 && count_in == prev_count && it >= 2) || act == 0) {
-      result = (count_in >= q) ? PFE_E_CAPACITY : PFE_OK;
-      break;
-    }
-    prev_count = count_in;
-  }
-  if (it > ctx->p_max_iters) it = ctx->p_max_iters;
-  // results: locked pairs inside [a, b], ascending
-  std::vector<int32_t> ord;
-  for (int32_t l = 0; l < nl; ++l)
-    if (lockLam[l] >= ctx->a && lockLam[l] <= ctx->b) ord.push_back(l);
-  std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return lockLam[x] < lockLam[y]; });
-  ctx->result_cols = ord;
-  ctx->result_lam.clear();
-  ctx->result_res.clear();
-  double maxres = 0.0;
-  for (int32_t l : ord) {
-    ctx->result_lam.push_back(lockLam[l]);
-    ctx->result_res.push_back(lockRes[l] * lmax);
-    maxres = std::max(maxres, lockRes[l]);
-  }
-  ctx->n_found = (int32_t)ord.size();
-  ctx->has_result = true;
-  ctx->stats.iterations = it;
-  ctx->stats.width = q;
-  ctx->stats.degree = ctx->m;
-  ctx->stats.n_found = ctx->n_found;
-  ctx->stats.matvecs = matvecs;
-  ctx->stats.lambda_max = lmax;
-  ctx->stats.count_estimate = ctx->has_count ? ctx->count_est : -1.0;
-  ctx->stats.window_estimate = window_est;
-  ctx->stats.kernel_launches = launch_count() - launches0;
-  ctx->stats.filter_launches = f_launch;
-  ctx->stats.filter_col_steps = f_cols64;
-  ctx->stats.filter_col_steps_f32 = f_cols32;
-  ctx->stats.seconds_filter_f32 = t_filter32;
-  ctx->stats.seconds_filter = t_filter;
-  ctx->stats.seconds_orth = t_orth;
-  ctx->stats.seconds_rr = t_rr;
-  ctx->stats.max_residual = maxres;
-  ctx->stats.fp64_sweeps = fp64_sweeps;
-  ctx->stats.status = (int32_t)result;
-  ctx->stats.seconds_total = now_s() - t_start;
-  if (n_found) *n_found = ctx->n_found;
-  if (result == PFE_E_CAPACITY) return pfe_fail(ctx, result, "every Ritz vector lies in [a, b]: raise PFE_P_WIDTH");
-  if (result == PFE_E_NOCONV) return pfe_fail(ctx, result, "iteration limit reached");
-  return PFE_OK;
+  return solve_finish(ctx, n_found);
 }
 
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *st) {
@@ -1101,12 +1324,61 @@ pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, co
 
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
   if (!ctxs || nsamples < 0) return PFE_E_ARG;
+  for (int32_t i = 0; i < nsamples; ++i)
+    if (!ctxs[i]) return PFE_E_ARG;
+  if (nsamples == 0) return PFE_OK;
+  pfe_ctx *c0 = ctxs[0];
+  for (int32_t i = 1; i < nsamples; ++i)
+    if (ctxs[i]->device != c0->device) return pfe_fail(c0, PFE_E_ARG, "batch contexts must share one device");
+  if (cudaSetDevice(c0->device) != cudaSuccess) return pfe_fail(c0, PFE_E_CUDA, "cudaSetDevice failed");
+  std::vector<pfe_status> status(nsamples, PFE_OK);
+  // set-up of every sample (filter design, width, buffers, start block)
+  for (int32_t i = 0; i < nsamples; ++i) status[i] = solve_setup(ctxs[i]);
+  BatchPlan plan;
+  pfe_status bst = batch_plan_init(c0, ctxs, nsamples, status, &plan);
+  if (bst != PFE_OK) {
+    batch_plan_free(&plan);
+    return bst;
+  }
+  for (int32_t i = 0; i < nsamples; ++i) ctxs[i]->solve.timed_filter = false;
+  double t_batch_filter = 0.0;
+  int64_t batch_replays = 0;
+  for (;;) {
+    bool any = false;
+    for (int32_t i = 0; i < nsamples; ++i)
+      if (status[i] == PFE_OK && !ctxs[i]->solve.done) any = true;
+    if (!any) break;
+    // 1. filter: one batched replay for the FP64 samples, the single-context path for FP32 ones
+    for (int32_t i = 0; i < nsamples; ++i) {
+      SolveState &st = ctxs[i]->solve;
+      if (status[i] != PFE_OK || st.done || st.use64) continue;
+      status[i] = solve_filter(ctxs[i]);
+    }
+    float ms = 0.f;
+    bst = batch_filter(c0, ctxs, nsamples, status, &plan, &ms);
+    if (bst != PFE_OK) {
+      batch_plan_free(&plan);
+      return bst;
+    }
+    t_batch_filter += ms * 1e-3;
+    ++batch_replays;
+    // 2. everything after the filter, per sample (its own stream waits for the batched filter)
+    for (int32_t i = 0; i < nsamples; ++i) {
+      SolveState &st = ctxs[i]->solve;
+      if (status[i] != PFE_OK || st.done) continue;
+      cudaStreamWaitEvent(ctxs[i]->stream, plan.done_ev, 0);
+      status[i] = solve_after_filter(ctxs[i]);
+    }
+  }
+  batch_plan_free(&plan);
   pfe_status first = PFE_OK;
   for (int32_t i = 0; i < nsamples; ++i) {
     int32_t nf = 0;
-    pfe_status st = ctxs[i] ? pfe_solve(ctxs[i], &nf) : PFE_E_ARG;
-    if (n_found) n_found[i] = nf;
-    if (st != PFE_OK && first == PFE_OK) first = st;
+    pfe_status fs = (status[i] == PFE_OK) ? solve_finish(ctxs[i], &nf) : status[i];
+    ctxs[i]->stats.seconds_filter = t_batch_filter;  // shared by the whole batch
+    ctxs[i]->stats.batch_replays = batch_replays;
+    if (n_found) n_found[i] = (status[i] == PFE_OK) ? nf : 0;
+    if (fs != PFE_OK && first == PFE_OK) first = fs;
   }
   return first;
 }

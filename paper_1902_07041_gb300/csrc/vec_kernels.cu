@@ -13,6 +13,7 @@ std::atomic<int64_t> g_launches{0};
 }
 int64_t launch_count() { return g_launches.load(); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t dbuf_reserve(DBuf &b, size_t bytes) {
   if (bytes <= b.bytes && b.p) return cudaSuccess;

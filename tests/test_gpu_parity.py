@@ -230,7 +230,10 @@ def test_solve_capacity_error():
 
 
 def test_solve_batch_equals_solo():
-    gs = [glassgen.generate(n, glassgen.subseed(3, i)) for i, n in enumerate((150, 220, 180))]
+    """Batched lockstep solve (one persistent filter launch per step over all samples, replayed from
+    a CUDA graph): every sample matches the exact interval eigenpairs and its own solo solve."""
+    sizes = (150, 420, 180, 300, 95)
+    gs = [glassgen.generate(n, glassgen.subseed(3, i)) for i, n in enumerate(sizes)]
     ctxs = []
     try:
         for g in gs:
@@ -239,12 +242,49 @@ def test_solve_batch_equals_solo():
             pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.15 * lmax)
             ctxs.append(ctx)
         nfs, st = pfe.pfe_solve_batch(ctxs)
-        assert st == pfe.PFE_OK
+        assert st == pfe.PFE_OK, [pfe.pfe_last_error(c) for c in ctxs]
+        for g, ctx, nf in zip(gs, ctxs, nfs):
+            lam, V, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
+            stats = pfe.pfe_get_stats(ctx)
+            assert stats["batch_replays"] >= 2
+            lmax = stats["lambda_max"]
+            H = oracle.csr_from_springs(g)
+            w, _, _ = oracle.exact_interval(H, 0.05 * lmax, 0.15 * lmax)
+            assert nf == w.size
+            assert np.allclose(lam, w, rtol=1e-10, atol=0)
+            assert np.all(oracle.residuals(H, lam, V) <= 1e-8 * lmax)
+            # the same sample solved alone
+            solo, _ = make_ctx(g)
+            try:
+                pfe.pfe_set_param(solo, pfe.PFE_P_LAMBDA_MAX, lmax)
+                pfe.pfe_set_interval(solo, 0.05 * lmax, 0.15 * lmax)
+                nf1, _ = pfe.pfe_solve(solo)
+                lam1, _, _ = pfe.pfe_get_eigenpairs(solo, g.n, nf1)
+            finally:
+                pfe.pfe_destroy(solo)
+            assert nf1 == nf and np.allclose(lam1, lam, rtol=1e-10, atol=0)
+    finally:
+        for c in ctxs:
+            pfe.pfe_destroy(c)
+
+
+def test_solve_batch_mixed_precision_members():
+    """A batch whose members use different filter precisions still matches the exact eigenpairs."""
+    gs = [glassgen.generate(n, 40 + i) for i, n in enumerate((200, 260))]
+    ctxs = []
+    try:
+        for i, g in enumerate(gs):
+            ctx, _ = make_ctx(g, PRECISION=i % 2)
+            lmax, _ = pfe.pfe_estimate(ctx)
+            pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.12 * lmax)
+            ctxs.append(ctx)
+        nfs, st = pfe.pfe_solve_batch(ctxs)
+        assert st == pfe.PFE_OK, [pfe.pfe_last_error(c) for c in ctxs]
         for g, ctx, nf in zip(gs, ctxs, nfs):
             lam, _, _ = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
             lmax = pfe.pfe_get_stats(ctx)["lambda_max"]
-            w, _, _ = oracle.exact_interval(oracle.csr_from_springs(g), 0.05 * lmax, 0.15 * lmax)
-            assert np.allclose(lam, w, rtol=1e-10, atol=0)
+            w, _, _ = oracle.exact_interval(oracle.csr_from_springs(g), 0.05 * lmax, 0.12 * lmax)
+            assert nf == w.size and np.allclose(lam, w, rtol=1e-10, atol=0)
     finally:
         for c in ctxs:
             pfe.pfe_destroy(c)
