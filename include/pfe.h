@@ -204,6 +204,25 @@ pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, co
                              const double *rhat, const double *vals_bar, double *k_bar, double *m_bar,
                              void *stream);
 
+/* The filter of pfe_filter_apply (FP64) without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library allocate device
+ * memory while they run -- applications whose device memory is already owned by another allocator
+ * (a framework's caching allocator, or a pool sized at start-up), and loops that cannot afford the
+ * implicit device synchronisation cudaMalloc and cudaFree may cause.
+ * Its work buffers live in one fixed device array of 4 Mi doubles (32 MiB) inside the library:
+ * every GPU that loads the library holds it until the process exits.  It needs
+ * 4 * n * round_up(k, 4) doubles; larger problems get PFE_E_CAPACITY and nothing runs.
+ * All calls share the array and it keeps the last call's contents; calls that overlap on the GPU
+ * (other streams or host threads) race on it, so the caller serialises them.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.
+ * Preconditions: the context already holds the FP64 filter operator for its current transform --
+ * any earlier pfe_filter_apply, pfe_estimate or pfe_solve on it builds it (else PFE_E_STATE).
+ * coeffs: host array of m + 1 coefficients (required); X, Y: device pointers, column-major n x k,
+ * ld >= n, float64; stream as in pfe_filter_apply. */
+pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const double *X,
+                                    int64_t ldx, double *Y, int64_t ldy, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batched solves of independent samples (the realisations H_1 .. H_8 of Sec. 4.2)
  * ------------------------------------------------------------------------------------- */

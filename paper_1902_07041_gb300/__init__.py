@@ -37,7 +37,7 @@ PFE_P_LANCZOS_STEPS, PFE_P_COUNT_DAMPING, PFE_P_MIN_WIDTH, PFE_P_REFINE_TOL = 15
 EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", "pfe_set_param",
            "pfe_get_param", "pfe_set_interval", "pfe_estimate", "pfe_get_filter", "pfe_solve",
            "pfe_get_eigenpairs", "pfe_get_stats", "pfe_filter_apply", "pfe_filter_adjoint",
-           "pfe_chain_springs", "pfe_solve_batch")
+           "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc")
 
 
 class PfeError(RuntimeError):
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "pfe_filter_adjoint": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _I64, _P, _I64, _P, _P]),
         "pfe_chain_springs": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P]),
         "pfe_solve_batch": (ctypes.c_int, [_P, _I32, _P]),
+        "pfe_filter_apply_noalloc": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _I64, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -276,3 +277,12 @@ def pfe_solve_batch(ctxs):
     nf = np.zeros(len(ctxs), np.int32)
     st = load().pfe_solve_batch(arr, len(ctxs), nf.ctypes.data)
     return [int(x) for x in nf], st
+
+
+def pfe_filter_apply_noalloc(ctx, m, coeffs, k, X, ldx, Y, ldy, stream=None):
+    """pfe_filter_apply (FP64) with its work buffers in the library's fixed device array: no device
+    allocation. Returns the status (raises on any status other than PFE_OK)."""
+    coeffs = _host(coeffs, np.float64)
+    st = load().pfe_filter_apply_noalloc(ctx, int(m), coeffs.ctypes.data, int(k), _dptr(X), int(ldx), _dptr(Y),
+                                         int(ldy), _stream(stream))
+    _check(st, ctx)
