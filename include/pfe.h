@@ -78,7 +78,13 @@ enum {
   PFE_P_LANCZOS_STEPS = 15, /* Lanczos steps of the lambda_max estimate (default 30) */
   PFE_P_COUNT_DAMPING = 16, /* damping of the estimator series (default 0: plain truncation) */
   PFE_P_MIN_WIDTH = 17,     /* lower bound on the automatic width (default 16) */
-  PFE_P_REFINE_TOL = 18     /* FP32 mode: residual below which FP64 sweeps take over (default 1e-6) */
+  PFE_P_REFINE_TOL = 18,    /* FP32 mode: residual below which FP64 sweeps take over (default 1e-6) */
+  PFE_P_STEP_SHAPE_F64 = 19, /* PROCESS-WIDE: kernel shape of the FP64 filter step, -1 = autotuned (default),
+                               0 warp per (atom, column chunk), 1 CTA per 8 atoms x chunk, 2 and 3: the
+                               same with two 3x3 blocks in flight per iteration, 4: neighbour rows staged
+                               in shared memory by cp.async four blocks ahead (16-byte lanes), 5 and 6:
+                               0 and 1 compiled for five resident CTAs per SM */
+  PFE_P_STEP_SHAPE_F32 = 20  /* PROCESS-WIDE: the same for the FP32 filter step */
 };
 
 /* ---------------------------------------------------------------------------------------

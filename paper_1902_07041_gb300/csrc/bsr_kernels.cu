@@ -8,6 +8,10 @@
 // 32 * CPL columns); each lane owns CPL adjacent columns and keeps 3 x CPL accumulators.
 // Block values and column indices are warp-uniform loads (served as L1 broadcasts); every
 // 3x3 block is read once per column chunk.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "pfe_internal.h"
 
 namespace pfe {
@@ -70,39 +74,62 @@ __device__ __forceinline__ void st_n(float *p, const float (&v)[4]) {
 // STEP : Z = alpha A X + beta W; Y += g1 Z                  (t_{j+1} = 2 Ht t_j - t_{j-1})
 // ADJ  : Z = alpha A X + beta W + g0 Y   (Y read-only)      (reverse sweep of the adjoint)
 // With A = (2/d)(H - cI) the step needs alpha = 1, beta = -1; the first step alpha = 1/2.
-template <typename T, int CPL, int MODE>
-__global__ void __launch_bounds__(256) k_bsr_step(int32_t n_atoms, const int32_t *__restrict__ rp,
+// GROUPED: the 8 warps of a CTA take 8 consecutive atoms of one column chunk (their neighbour
+// rows overlap, so gathers hit L1); otherwise a warp takes (atom, chunk) with chunk fastest.
+// UNROLL = 2: two blocks per iteration, so six row gathers are in flight per lane.
+template <typename T, int CPL, int MODE, bool GROUPED, int UNROLL, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) k_bsr_step(int32_t n_atoms, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, const T *__restrict__ vals,
                                                   int32_t k, int64_t ld, int32_t nchunk, const T *__restrict__ X,
                                                   const T *W, T *Z, T *Y, T alpha, T beta, T g0, T g1) {
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t atom = gw / nchunk;
+  int64_t atom;
+  int chunk;
+  if (GROUPED) {
+    const int64_t b = blockIdx.x;
+    chunk = (int)(b % nchunk);
+    atom = (b / nchunk) * 8 + (threadIdx.x >> 5);
+  } else {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    atom = gw / nchunk;
+    chunk = (int)(gw - atom * nchunk);
+  }
   if (atom >= n_atoms) return;
-  const int chunk = (int)(gw - atom * nchunk);
   const int c0 = (chunk * 32 + lane) * CPL;
   const bool on = c0 < k;
   T acc[3][CPL];
 #pragma unroll
   for (int c = 0; c < CPL; ++c) acc[0][c] = acc[1][c] = acc[2][c] = T(0);
   const int p0 = __ldg(rp + atom), p1 = __ldg(rp + atom + 1);
-  for (int p = p0; p < p1; ++p) {
-    const int64_t j = __ldg(ci + p);
-    const T *v = vals + 9 * (int64_t)p;
-    T a[9];
+  for (int p = p0; p < p1; p += UNROLL) {
+    T a[UNROLL][9];
+    T x[UNROLL][3][CPL];
+    bool has[UNROLL];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) a[t] = __ldg(v + t);
+    for (int u = 0; u < UNROLL; ++u) {
+      has[u] = (p + u) < p1;
+      const int pu = has[u] ? p + u : p;
+      const int64_t j = __ldg(ci + pu);
+      const T *v = vals + 9 * (int64_t)pu;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) a[u][t] = __ldg(v + t);
+      if (on) {
+        const T *xr = X + 3 * j * ld + c0;
+        ldg_n(xr, x[u][0]);
+        ldg_n(xr + ld, x[u][1]);
+        ldg_n(xr + 2 * ld, x[u][2]);
+      }
+    }
     if (on) {
-      const T *xr = X + 3 * j * ld + c0;
-      T x0[CPL], x1[CPL], x2[CPL];
-      ldg_n(xr, x0);
-      ldg_n(xr + ld, x1);
-      ldg_n(xr + 2 * ld, x2);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        acc[0][c] = fma(a[0], x0[c], fma(a[1], x1[c], fma(a[2], x2[c], acc[0][c])));
-        acc[1][c] = fma(a[3], x0[c], fma(a[4], x1[c], fma(a[5], x2[c], acc[1][c])));
-        acc[2][c] = fma(a[6], x0[c], fma(a[7], x1[c], fma(a[8], x2[c], acc[2][c])));
+      for (int u = 0; u < UNROLL; ++u) {
+        if (!has[u]) continue;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          acc[0][c] = fma(a[u][0], x[u][0][c], fma(a[u][1], x[u][1][c], fma(a[u][2], x[u][2][c], acc[0][c])));
+          acc[1][c] = fma(a[u][3], x[u][0][c], fma(a[u][4], x[u][1][c], fma(a[u][5], x[u][2][c], acc[1][c])));
+          acc[2][c] = fma(a[u][6], x[u][0][c], fma(a[u][7], x[u][1][c], fma(a[u][8], x[u][2][c], acc[2][c])));
+        }
       }
     }
   }
@@ -127,10 +154,113 @@ __global__ void __launch_bounds__(256) k_bsr_step(int32_t n_atoms, const int32_t
     }
     st_n(Z + off, z);
     if (MODE == MODE_FIRST) {
-      T x[CPL], y[CPL];
-      ldg_n(X + off, x);
+      T xo[CPL], y[CPL];
+      ldg_n(X + off, xo);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], g0 * x[c]);
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], g0 * xo[c]);
+      st_n(Y + off, y);
+    } else if (MODE == MODE_STEP && Y != nullptr) {
+      T y[CPL];
+      ld_n(Y + off, y);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      st_n(Y + off, y);
+    }
+  }
+}
+
+// Shape 4: the neighbour rows are staged in shared memory by asynchronous copies (cp.async),
+// STAGES blocks ahead of the FMAs, in a ring private to each warp.  Each lane copies and later
+// reads only its own 16 bytes of every row, so no warp-level barrier is needed; the copies keep
+// STAGES x 3 row gathers in flight per warp without holding registers.  Needs 16-byte lanes
+// (float x 4 or double x 2).
+constexpr int kStages = 4;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <typename T, int CPL, int MODE>
+__global__ void __launch_bounds__(256) k_bsr_step_async(int32_t n_atoms, const int32_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci, const T *__restrict__ vals,
+                                                        int32_t k, int64_t ld, int32_t nchunk, const T *__restrict__ X,
+                                                        const T *W, T *Z, T *Y, T alpha, T beta, T g0, T g1) {
+  static_assert(sizeof(T) * CPL == 16, "16-byte lanes");
+  __shared__ __align__(16) T ring[8][kStages][3][32 * CPL];  // [warp][stage][row][lane * CPL]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t atom = gw / nchunk;
+  if (atom >= n_atoms) return;
+  const int chunk = (int)(gw - atom * nchunk);
+  const int c0 = (chunk * 32 + lane) * CPL;
+  const bool on = c0 < k;
+  T acc[3][CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) acc[0][c] = acc[1][c] = acc[2][c] = T(0);
+  const int p0 = __ldg(rp + atom), nb = __ldg(rp + atom + 1) - p0;
+  auto issue = [&](int b) {
+    if (b < nb && on) {
+      const int64_t j = __ldg(ci + p0 + b);
+      const T *xr = X + 3 * j * ld + c0;
+      T *dst = &ring[warp][b % kStages][0][lane * CPL];
+      cp_async16(dst, xr);
+      cp_async16(dst + 32 * CPL, xr + ld);
+      cp_async16(dst + 64 * CPL, xr + 2 * ld);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int b = 0; b < kStages - 1; ++b) issue(b);
+  for (int b = 0; b < nb; ++b) {
+    issue(b + kStages - 1);
+    cp_async_wait<kStages - 1>();
+    const T *v = vals + 9 * (int64_t)(p0 + b);
+    T a[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) a[t] = __ldg(v + t);
+    if (on) {
+      const T *src = &ring[warp][b % kStages][0][lane * CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const T x0 = src[c], x1 = src[32 * CPL + c], x2 = src[64 * CPL + c];
+        acc[0][c] = fma(a[0], x0, fma(a[1], x1, fma(a[2], x2, acc[0][c])));
+        acc[1][c] = fma(a[3], x0, fma(a[4], x1, fma(a[5], x2, acc[1][c])));
+        acc[2][c] = fma(a[6], x0, fma(a[7], x1, fma(a[8], x2, acc[2][c])));
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!on) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int64_t off = (3 * atom + r) * ld + c0;
+    T z[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) z[c] = alpha * acc[r][c];
+    if (MODE == MODE_STEP || MODE == MODE_ADJ) {
+      T w[CPL];
+      ld_n(W + off, w);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) z[c] = fma(beta, w[c], z[c]);
+    }
+    if (MODE == MODE_ADJ) {
+      T y[CPL];
+      ld_n(Y + off, y);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) z[c] = fma(g0, y[c], z[c]);
+    }
+    st_n(Z + off, z);
+    if (MODE == MODE_FIRST) {
+      T xo[CPL], y[CPL];
+      ldg_n(X + off, xo);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], g0 * xo[c]);
       st_n(Y + off, y);
     } else if (MODE == MODE_STEP && Y != nullptr) {
       T y[CPL];
@@ -143,38 +273,166 @@ __global__ void __launch_bounds__(256) k_bsr_step(int32_t n_atoms, const int32_t
 }
 
 template <typename T, int CPL>
+void dispatch_async(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
+                    T beta, T g0, T g1, cudaStream_t s) {
+  const int32_t nchunk = (k + 32 * CPL - 1) / (32 * CPL);
+  const int64_t blocks = ((int64_t)A.n_atoms * nchunk * 32 + 255) / 256;
+#define PFE_ASYNC_LAUNCH(M)                                                                                 \
+  PFE_LAUNCH k_bsr_step_async<T, CPL, M><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, \
+                                                                           nchunk, X, W, Z, Y, alpha, beta, g0, g1)
+  if (mode == MODE_SPMM)
+    PFE_ASYNC_LAUNCH(MODE_SPMM);
+  else if (mode == MODE_FIRST)
+    PFE_ASYNC_LAUNCH(MODE_FIRST);
+  else if (mode == MODE_ADJ)
+    PFE_ASYNC_LAUNCH(MODE_ADJ);
+  else
+    PFE_ASYNC_LAUNCH(MODE_STEP);
+#undef PFE_ASYNC_LAUNCH
+}
+
+template <typename T, int CPL, bool GROUPED, int UNROLL, int MINB = 1>
 void dispatch_mode(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
                    T beta, T g0, T g1, cudaStream_t s) {
   const int32_t nchunk = (k + 32 * CPL - 1) / (32 * CPL);
-  const int64_t threads = (int64_t)A.n_atoms * nchunk * 32;
-  const int64_t blocks = (threads + 255) / 256;
+  const int64_t blocks = GROUPED ? ((int64_t)A.n_atoms + 7) / 8 * nchunk
+                                 : ((int64_t)A.n_atoms * nchunk * 32 + 255) / 256;
+#define PFE_STEP_LAUNCH(M)                                                                                 \
+  PFE_LAUNCH k_bsr_step<T, CPL, M, GROUPED, UNROLL, MINB><<<(unsigned)blocks, 256, 0, s>>>(               \
+      A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W, Z, Y, alpha, beta, g0, g1)
   if (mode == MODE_SPMM)
-    PFE_LAUNCH k_bsr_step<T, CPL, MODE_SPMM><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
-                                                                  Z, Y, alpha, beta, g0, g1);
+    PFE_STEP_LAUNCH(MODE_SPMM);
   else if (mode == MODE_FIRST)
-    PFE_LAUNCH k_bsr_step<T, CPL, MODE_FIRST><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X,
-                                                                   W, Z, Y, alpha, beta, g0, g1);
+    PFE_STEP_LAUNCH(MODE_FIRST);
   else if (mode == MODE_ADJ)
-    PFE_LAUNCH k_bsr_step<T, CPL, MODE_ADJ><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
-                                                                 Z, Y, alpha, beta, g0, g1);
+    PFE_STEP_LAUNCH(MODE_ADJ);
   else
-    PFE_LAUNCH k_bsr_step<T, CPL, MODE_STEP><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, A.rp, A.ci, A.vals, k, ld, nchunk, X, W,
-                                                                  Z, Y, alpha, beta, g0, g1);
+    PFE_STEP_LAUNCH(MODE_STEP);
+#undef PFE_STEP_LAUNCH
+}
+
+template <typename T, int CPL>
+void dispatch_variant(int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
+                      T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s) {
+  switch (variant) {
+    case 1: dispatch_mode<T, CPL, true, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 2: dispatch_mode<T, CPL, false, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 3: dispatch_mode<T, CPL, true, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 5: dispatch_mode<T, CPL, false, 1, 5>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 6: dispatch_mode<T, CPL, true, 1, 5>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 4:
+      if constexpr (sizeof(T) * CPL == 16)
+        dispatch_async<T, CPL>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+      else
+        dispatch_mode<T, CPL, false, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+      break;
+    default: dispatch_mode<T, CPL, false, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+  }
 }
 
 bool aligned(const void *p, size_t a) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 }  // namespace
 
+// Kernel shape of the fused step: 0 = warp per (atom, chunk), 1 = CTA per 8 atoms x chunk,
+// 2 = as 0 with two blocks in flight, 3 = as 1 with two blocks in flight, 4 = rows staged in
+// shared memory by cp.async, four blocks ahead (16-byte lanes only; else shape 0), 5 and 6 = as
+// 0 and 1 compiled for five resident CTAs per SM (at most 51 registers a thread).
+// A forced shape (set_step_variant) wins; otherwise the autotuner's choice for (type, columns per
+// lane, column chunks) is used, and the default 0 before any tuning.
+namespace {
+constexpr int kVariants = 7;
+int g_forced[2] = {-1, -1};  // [double, float]
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;  // (is_float, CPL, min(nchunk, 16)) -> shape
+
+int pick_variant(int is_float, int cpl, int32_t nchunk) {
+  if (g_forced[is_float] >= 0) return g_forced[is_float];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(is_float, cpl, std::min(nchunk, 16)));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+}  // namespace
+
+void set_step_variant(int is_float, int variant) { g_forced[is_float ? 1 : 0] = variant; }
+int step_variant(int is_float) { return g_forced[is_float ? 1 : 0]; }
+
+namespace {
+template <typename T>
+int cpl_for(int32_t k, int64_t ld, bool al16, bool al8);
+template <>
+int cpl_for<double>(int32_t k, int64_t ld, bool al16, bool) { return (k > 32 && ld % 2 == 0 && al16) ? 2 : 1; }
+template <>
+int cpl_for<float>(int32_t k, int64_t ld, bool al16, bool al8) {
+  return (k > 64 && ld % 4 == 0 && al16) ? 4 : (k > 32 && ld % 2 == 0 && al8) ? 2 : 1;
+}
+
+template <typename T>
+void dispatch_cpl(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
+                  T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s) {
+  if (cpl == 4)
+    dispatch_variant<T, (sizeof(T) == 4 ? 4 : 2)>(variant, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  else if (cpl == 2)
+    dispatch_variant<T, 2>(variant, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  else
+    dispatch_variant<T, 1>(variant, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+}
+}  // namespace
+
+// Autotuner of the step's kernel shape: times every shape as a plain product X -> scratch (the
+// scratch is overwritten afterwards) and keeps the fastest for this (type, CPL, chunk count).
+template <typename T>
+void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, cudaStream_t s) {
+  if (k <= 0 || A.n_atoms <= 0) return;
+  const int is_float = sizeof(T) == 4;
+  if (g_forced[is_float] >= 0) return;
+  const int cpl = cpl_for<T>(k, ld, aligned(X, 16) && aligned(scratch, 16), aligned(X, 8) && aligned(scratch, 8));
+  const int32_t nchunk = (k + 32 * cpl - 1) / (32 * cpl);
+  const auto key = std::make_tuple(is_float, cpl, std::min(nchunk, 16));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tuned.count(key)) return;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  float best = 1e30f;
+  int best_v = 0;
+  for (int v = 0; v < kVariants; ++v) {
+    float t = 1e30f;
+    for (int trial = 0; trial < 2; ++trial) {
+      cudaEventRecord(e0, s);
+      dispatch_cpl<T>(cpl, v, A, MODE_SPMM, k, ld, X, nullptr, scratch, nullptr, T(1), T(0), T(0), T(0), s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (trial == 1) t = ms;
+    }
+    if (t < best) {
+      best = t;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best_v;
+}
+template void tune_step<double>(const Bsr<double> &, int32_t, int64_t, const double *, double *, cudaStream_t);
+template void tune_step<float>(const Bsr<float> &, int32_t, int64_t, const float *, float *, cudaStream_t);
+
 template <>
 void launch_bsr_step<double>(const Bsr<double> &A, int mode, int32_t k, int64_t ld, const double *X, const double *W,
                              double *Z, double *Y, double alpha, double beta, double g0, double g1, cudaStream_t s) {
   if (k <= 0 || A.n_atoms <= 0) return;
-  const bool v2 = k > 32 && ld % 2 == 0 && aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
-  if (v2)
-    dispatch_mode<double, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
-  else
-    dispatch_mode<double, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
+  const int cpl = cpl_for<double>(k, ld, al16, false);
+  const int v = pick_variant(0, cpl, (k + 32 * cpl - 1) / (32 * cpl));
+  dispatch_cpl<double>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
 template <>
@@ -183,12 +441,9 @@ void launch_bsr_step<float>(const Bsr<float> &A, int mode, int32_t k, int64_t ld
   if (k <= 0 || A.n_atoms <= 0) return;
   const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
   const bool al8 = aligned(X, 8) && aligned(W, 8) && aligned(Z, 8) && aligned(Y, 8);
-  if (k > 64 && ld % 4 == 0 && al16)
-    dispatch_mode<float, 4>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
-  else if (k > 32 && ld % 2 == 0 && al8)
-    dispatch_mode<float, 2>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
-  else
-    dispatch_mode<float, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+  const int cpl = cpl_for<float>(k, ld, al16, al8);
+  const int v = pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl));
+  dispatch_cpl<float>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
 // ---- a0: mass weighting, one warp per atom row ----------------------------------------

@@ -56,6 +56,12 @@ enum StepMode { MODE_SPMM = 0, MODE_FIRST = 1, MODE_STEP = 2, MODE_ADJ = 3 };
 template <typename T>
 void launch_bsr_step(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
                      T beta, T g0, T g1, cudaStream_t s);
+// kernel shape of the fused step (see bsr_kernels.cu): forced shape (-1 = autotuned) and the
+// autotuner, which times every shape once per (type, columns per lane, chunk count)
+void set_step_variant(int is_float, int variant);
+int step_variant(int is_float);
+template <typename T>
+void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, cudaStream_t s);
 
 // a0: H = Delta / sqrt(m_i m_j) per block; also the row index of each block
 void launch_mass_weight(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *delta, const double *mass,
@@ -103,6 +109,8 @@ template <typename T>
 void launch_rowmajor_to_colmajor(int64_t n, int32_t k, const T *R, int64_t ldr, T *C, int64_t ldc, cudaStream_t s);
 template <typename T>
 void launch_zero(T *p, int64_t count, cudaStream_t s);
+// *out = max |G - I| over a k x k matrix (device scalar)
+void launch_max_dev_identity(int32_t k, const double *G, double *out, cudaStream_t s);
 
 // Batched filter: one persistent launch per Chebyshev step over every sample's work items.
 // One descriptor per sample (device-resident, refreshed before every graph replay).

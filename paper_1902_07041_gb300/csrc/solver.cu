@@ -71,6 +71,7 @@ pfe_status run_filter(pfe_ctx *ctx, const Bsr<T> &A, const double *coef, int32_t
     launch_axpby<T>(ctx->n, k, (T)coef[0], X, ld, T(0), Y, ld, s);
     return check_launch(ctx, "filter (degree 0)");
   }
+  tune_step<T>(A, k, ld, X, b1, s);  // b1 is free until the second step
   launch_bsr_step<T>(A, MODE_FIRST, k, ld, X, nullptr, b0, Y, T(0.5), T(0), (T)coef[0], (T)coef[1], s);
   const T *tprev = X;
   T *tcur = b0;
@@ -265,32 +266,31 @@ pfe_status window_estimate(pfe_ctx *ctx, double *out) {
 }
 
 // ---------------------------------------------------------------- CholQR2 (+ shifted retry)
-// One CholeskyQR pass: G = Y^T Y (DMMA Gram), R^T R = G (cuSOLVER potrf on the k x k matrix),
-// Out = Y R^{-1} (R^{-1} by a k x k triangular solve, then a DMMA block update).
-pfe_status cholqr(pfe_ctx *ctx, const double *Y, double *Out, int32_t k, int64_t ld, bool *broke) {
+// G = Y^T Y by the DMMA Gram kernel (upper tiles, mirrored)
+pfe_status gram_sym(pfe_ctx *ctx, const double *Y, int32_t k, int64_t ld, double *G) {
+  RESERVE(double, gw, ctx->w_gram, gram_work(ctx->n, k, k, true));
+  launch_gram(ctx->n, k, k, Y, ld, Y, ld, 1.0, 0.0, G, k, true, gw, ctx->stream);
+  return check_launch(ctx, "Gram");
+}
+
+// R^T R = G (cuSOLVER potrf, upper) with the shifted retry of Fukaya et al. (2020): G + s I,
+// s = 11 (n k + k (k + 1)) u trace(G); then Rinv = R^{-1} by a k x k triangular solve.
+pfe_status chol_factor(pfe_ctx *ctx, double *G, double *Rinv, int32_t k, bool *shifted) {
   const int64_t n = ctx->n;
   cudaStream_t s = ctx->stream;
-  RESERVE(double, G, ctx->w_small, (size_t)2 * k * k);
-  double *Rinv = G + (size_t)k * k;
   RESERVE(int, info, ctx->w_info, 4);
-  RESERVE(double, gw, ctx->w_gram, gram_work(n, k, k, true));
   int lwork = 0;
   PFE_SOLVER_TRY(ctx, cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, &lwork));
   RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lwork, 1));
-  launch_gram(n, k, k, Y, ld, Y, ld, 1.0, 0.0, G, k, true, gw, s);
-  PFE_TRY(check_launch(ctx, "Gram"));
+  std::vector<double> hG((size_t)k * k);
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
   PFE_SOLVER_TRY(ctx, cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k, G, k, work, lwork, info));
   int hinfo = 0;
   PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
   PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  *broke = false;
+  *shifted = false;
   if (hinfo != 0) {
-    // shifted CholeskyQR (Fukaya et al. 2020): G + s I with s = 11 (n k + k (k + 1)) u trace(G)
-    *broke = true;
-    launch_gram(n, k, k, Y, ld, Y, ld, 1.0, 0.0, G, k, true, gw, s);
-    std::vector<double> hG((size_t)k * k);
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), G, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    *shifted = true;
     double tr = 0.0;
     for (int32_t i = 0; i < k; ++i) tr += hG[(size_t)i * k + i];
     const double sh = 11.0 * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
@@ -301,44 +301,59 @@ pfe_status cholqr(pfe_ctx *ctx, const double *Y, double *Out, int32_t k, int64_t
     PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hinfo != 0) return pfe_fail(ctx, PFE_E_BREAKDOWN, "CholeskyQR broke down even with a shift");
   }
-  // R^{-1}: solve R Z = I (k x k, upper triangular)
-  {
-    std::vector<double> eye((size_t)k * k, 0.0);
-    for (int32_t i = 0; i < k; ++i) eye[(size_t)i * k + i] = 1.0;
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(Rinv, eye.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
-    const double one = 1.0;
-    PFE_BLAS_TRY(ctx, cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
-                                  CUBLAS_DIAG_NON_UNIT, k, k, &one, G, k, Rinv, k));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // eye must outlive its copy
-  }
-  launch_update(n, k, k, Y, ld, Rinv, k, 1.0, 0.0, Out, ld, s);
-  return check_launch(ctx, "CholeskyQR update");
+  std::vector<double> eye((size_t)k * k, 0.0);
+  for (int32_t i = 0; i < k; ++i) eye[(size_t)i * k + i] = 1.0;
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(Rinv, eye.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
+  const double one = 1.0;
+  PFE_BLAS_TRY(ctx, cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT,
+                                k, k, &one, G, k, Rinv, k));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // eye must outlive its copy
+  return PFE_OK;
 }
 
-// CholQR2 of Y using tmp as the second buffer; *result points to the buffer holding Q.
+// CholQR2 of Y into an orthonormal Q (Y is n x k, row-major, row stride ld), using tmp as the
+// second buffer; *result points to whichever holds Q.  Pass 1: G = Y^T Y, Y R^{-1} -> tmp.
+// Pass 2 only if the Gram matrix of tmp deviates from I by more than 1e-13 (max entry), and
+// a third pass after a shifted factorisation.
 pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result) {
   *result = Y;
   if (k <= 0) return PFE_OK;
-  bool broke = false;
-  PFE_TRY(cholqr(ctx, Y, tmp, k, ld, &broke));
-  PFE_TRY(cholqr(ctx, tmp, Y, k, ld, &broke));
-  if (broke) {
-    PFE_TRY(cholqr(ctx, Y, tmp, k, ld, &broke));
-    *result = tmp;
+  cudaStream_t s = ctx->stream;
+  RESERVE(double, G, ctx->w_small, (size_t)2 * k * k + 8);
+  double *Rinv = G + (size_t)k * k, *dev = G + 2 * (size_t)k * k;
+  double *src = Y, *dst = tmp;
+  bool any_shift = false;
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass == 2 && !any_shift) break;  // the third pass only follows a shifted factorisation
+    PFE_TRY(gram_sym(ctx, src, k, ld, G));
+    if (pass > 0) {
+      launch_max_dev_identity(k, G, dev, s);
+      double h = 1.0;
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+      if (h <= 1e-13 && !(any_shift && pass == 1)) break;
+    }
+    bool shifted = false;
+    PFE_TRY(chol_factor(ctx, G, Rinv, k, &shifted));
+    any_shift = any_shift || shifted;
+    launch_update(ctx->n, k, k, src, ld, Rinv, k, 1.0, 0.0, dst, ld, s);
+    PFE_TRY(check_launch(ctx, "CholeskyQR update"));
+    *result = dst;
+    std::swap(src, dst);
   }
   return PFE_OK;
 }
 
-// Y <- Y - L (L^T Y), twice (classical Gram-Schmidt against the locked block), DMMA products
+// Y <- Y - L (L^T Y): one classical Gram-Schmidt pass against the locked block (DMMA products).
+// The locked vectors are converged eigenvectors and the active block was orthogonal to them before
+// the filter, so the filtered block's component along them is small and one pass suffices.
 pfe_status project_out(pfe_ctx *ctx, const double *L, int32_t nl, double *Y, int32_t k, int64_t ld) {
   if (nl <= 0 || k <= 0) return PFE_OK;
   const int64_t n = ctx->n;
   RESERVE(double, h, ctx->w_small2, (size_t)nl * k);
   RESERVE(double, gw, ctx->w_gram, gram_work(n, nl, k, false));
-  for (int pass = 0; pass < 2; ++pass) {
-    launch_gram(n, nl, k, L, ld, Y, ld, 1.0, 0.0, h, nl, false, gw, ctx->stream);
-    launch_update(n, k, nl, L, ld, h, nl, -1.0, 1.0, Y, ld, ctx->stream);
-  }
+  launch_gram(n, nl, k, L, ld, Y, ld, 1.0, 0.0, h, nl, false, gw, ctx->stream);
+  launch_update(n, k, nl, L, ld, h, nl, -1.0, 1.0, Y, ld, ctx->stream);
   return check_launch(ctx, "projection");
 }
 
@@ -476,8 +491,9 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
                                        st.evals, work, lw, st.info));
   launch_update(n, act, act, st.X, ld, st.A, act, 1.0, 0.0, st.Y, ld, s);
   std::swap(st.X, st.Y);
-  launch_update(n, act, act, st.W, ld, st.A, act, 1.0, 0.0, st.T0, ld, s);
-  std::swap(st.W, st.T0);
+  // W = H X again on the rotated block: one BSR product instead of the n x q x q update W <- W Q
+  launch_bsr_step<double>(bsr_H(ctx), MODE_SPMM, act, ld, st.X, nullptr, st.W, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+  st.matvecs += act;
   launch_col_resid2(n, act, st.W, st.X, ld, st.evals, st.resid2, st.red, s);
   PFE_TRY(check_launch(ctx, "residuals"));
   cudaEventRecord(st.ev[3], s);
@@ -1057,6 +1073,12 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!(v > 0)) return pfe_fail(ctx, PFE_E_ARG, "REFINE_TOL must be > 0");
       ctx->p_refine_tol = v;
       break;
+    case PFE_P_STEP_SHAPE_F64:
+    case PFE_P_STEP_SHAPE_F32:
+      if (!(v == -1 || (v >= 0 && v <= 6 && v == std::floor(v))))
+        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..6");
+      set_step_variant(key == PFE_P_STEP_SHAPE_F32, (int)v);
+      break;
     default:
       return pfe_fail(ctx, PFE_E_ARG, "unknown parameter key " + std::to_string(key));
   }
@@ -1084,6 +1106,8 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_COUNT_DAMPING: *v = ctx->p_count_damping; break;
     case PFE_P_MIN_WIDTH: *v = ctx->p_min_width; break;
     case PFE_P_REFINE_TOL: *v = ctx->p_refine_tol; break;
+    case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
+    case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;
   }
   return PFE_OK;

@@ -187,7 +187,29 @@ __global__ void k_row_to_col(int64_t n, int32_t k, const T *__restrict__ R, int6
 
 inline unsigned grid1(int64_t total, int threads = 256) { return (unsigned)((total + threads - 1) / threads); }
 
+// out = max_ij |G_ij - delta_ij| over a k x k matrix, one block
+__global__ void k_max_dev_identity(int32_t k, const double *__restrict__ G, double *out) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int64_t i = t / k, j = t - i * k;
+    m = fmax(m, fabs(G[t] - (i == j ? 1.0 : 0.0)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+void launch_max_dev_identity(int32_t k, const double *G, double *out, cudaStream_t s) {
+  PFE_LAUNCH k_max_dev_identity<<<1, 1024, 0, s>>>(k, G, out);
+}
 
 template <typename T>
 void launch_fill_normal(uint64_t seed, uint32_t stream_id, int64_t n, int32_t k, int32_t col0, T *X, int64_t ld,

@@ -26,12 +26,14 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--degree", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--shape", type=int, default=-1, help="kernel shape 0..3, -1 = autotuned")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
     rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
     ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
     try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_STEP_SHAPE_F64 if a.dtype == "f64" else pfe.PFE_P_STEP_SHAPE_F32, a.shape)
         pfe.pfe_estimate(ctx)
         tdt = torch.float64 if a.dtype == "f64" else torch.float32
         dt = pfe.PFE_F64 if a.dtype == "f64" else pfe.PFE_F32
@@ -58,7 +60,7 @@ def main():
             times[m] = best
         for r in range(a.reps):
             per = (times[a.degree + 1][r] - times[1][r]) / a.degree
-            print(json.dumps({"n_atoms": g.n_atoms, "k": a.k, "dtype": a.dtype, "s_per_step": per,
+            print(json.dumps({"n_atoms": g.n_atoms, "k": a.k, "dtype": a.dtype, "shape": a.shape, "s_per_step": per,
                               "alg_gbs": step_bytes / per / 1e9, "alg_gflops": step_flops / per / 1e9}), flush=True)
     finally:
         pfe.pfe_destroy(ctx)

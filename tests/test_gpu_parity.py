@@ -90,6 +90,26 @@ def test_filter_fp64_parity(N, seed, k, m):
         pfe.pfe_destroy(ctx)
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+def test_filter_every_kernel_shape(shape):
+    """Each kernel shape of the fused step (forced instead of autotuned), FP64 and FP32, ragged k."""
+    g = glassgen.generate(333, 13)
+    ctx, _ = make_ctx(g, LAMBDA_MAX=0.25)
+    try:
+        coef = oracle.filter_coeffs(-0.95, -0.9, 0.02, 21, "none")
+        ref_c = oracle.csr_from_springs(g)
+        for dt, key, tol in ((pfe.PFE_F64, "STEP_SHAPE_F64", 1e-11), (pfe.PFE_F32, "STEP_SHAPE_F32", 2e-4)):
+            pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), shape)
+            for k in (7, 45, 133):
+                X = np.random.default_rng(k).standard_normal((g.n, k))
+                Y = filter_gpu(ctx, coef, X, dt)
+                ref = oracle.cheb_filter(ref_c, 0.125, 0.125, coef, X)
+                assert np.max(np.abs(Y - ref)) <= tol * np.abs(X).max() * np.abs(coef).sum(), (dt, k)
+            pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), -1)
+    finally:
+        pfe.pfe_destroy(ctx)
+
+
 def test_filter_first_step_is_transformed_hessian():
     """Coefficients e_1 give Ht X = (H - cI)/d X: mass weighting (a0) and the transform."""
     g = glassgen.generate(200, 9)
