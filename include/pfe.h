@@ -68,7 +68,8 @@ enum {
                                estimate + 8, MIN_WIDTH), the window being [a - eps, b + eps] (default 0) */
   PFE_P_WIDTH_FACTOR = 6,   /* default 1.5 */
   PFE_P_TOL = 7,            /* residual tolerance ||H v - lambda v|| / lambda_max_est (default 1e-8) */
-  PFE_P_PRECISION = 8,      /* filter precision: 0 FP64 (default), 1 FP32 with FP64 refinement */
+  PFE_P_PRECISION = 8,      /* filter precision: 0 FP64 (default); 1 mixed: each Ritz pair is filtered in
+                               FP32 while its residual exceeds REFINE_TOL, in FP64 after */
   PFE_P_MAX_ITERS = 9,      /* subspace-iteration limit (default 60) */
   PFE_P_SEED = 10,          /* seed of the random start block and estimator vectors (default 0) */
   PFE_P_LAMBDA_MAX = 11,    /* spectrum upper bound; 0 = estimate by Lanczos (default 0) */
@@ -78,7 +79,7 @@ enum {
   PFE_P_LANCZOS_STEPS = 15, /* Lanczos steps of the lambda_max estimate (default 30) */
   PFE_P_COUNT_DAMPING = 16, /* damping of the estimator series (default 0: plain truncation) */
   PFE_P_MIN_WIDTH = 17,     /* lower bound on the automatic width (default 16) */
-  PFE_P_REFINE_TOL = 18,    /* FP32 mode: residual below which FP64 sweeps take over (default 1e-6) */
+  PFE_P_REFINE_TOL = 18,    /* mixed mode: residual below which a pair's filter runs in FP64 (default 1e-4) */
   PFE_P_STEP_SHAPE_F64 = 19, /* PROCESS-WIDE: kernel shape of the FP64 filter step, -1 = autotuned (default),
                                0 warp per (atom, column chunk), 1 CTA per 8 atoms x chunk, 2 and 3: the
                                same with two 3x3 blocks in flight per iteration, 4: neighbour rows staged
@@ -165,7 +166,7 @@ typedef struct {
   double seconds_orth;
   double seconds_rr;
   double max_residual;
-  int32_t fp64_sweeps; /* FP32 mode: iterations run with the FP64 filter */
+  int32_t fp64_sweeps; /* iterations in which some columns used the FP64 filter */
   int32_t status;
   double window_estimate; /* estimated eigenvalue count of the margin window (automatic width only) */
   int64_t kernel_launches;     /* launches of this library's own kernels since the context was created

@@ -164,8 +164,9 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
 // State of one filtered subspace iteration (kept in the context between stages)
 // --------------------------------------------------------------------------------------
 struct SolveState {
-  bool fp32 = false, use64 = true, was64 = true, done = false, timed_filter = true;
+  bool fp32 = false, use64 = true, was64 = true, done = false, timed_filter = true, timed32 = false;
   int32_t q = 0, act = 0, nl = 0, it = 0, prev_count = -1, fp64_sweeps = 0;
+  int32_t k64 = 0;  // mixed precision: the first k64 active columns use the FP64 filter
   int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
   double t_start = 0, t_filter = 0, t_filter32 = 0, t_orth = 0, t_rr = 0, prev_worst = 1e300, window_est = -1.0;
   pfe_status result = PFE_E_NOCONV;
@@ -176,6 +177,7 @@ struct SolveState {
   float *X32 = nullptr, *Y32 = nullptr, *B32a = nullptr, *B32b = nullptr;
   std::vector<double> lockLam, lockRes, hth, hr2;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev32[2] = {nullptr, nullptr};
 };
 
 // --------------------------------------------------------------------------------------
@@ -209,7 +211,7 @@ struct pfe_ctx {
   int32_t p_count_m = 30, p_count_degree = 100, p_lanczos_steps = 30;
   int p_count_damping = 0;
   int32_t p_min_width = 16;
-  double p_refine_tol = 1e-6;
+  double p_refine_tol = 1e-4;
 
   // state
   bool has_interval = false;

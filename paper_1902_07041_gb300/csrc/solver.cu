@@ -367,6 +367,8 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   SolveState &st = ctx->solve;
   for (int e = 0; e < 4; ++e)
     if (st.ev[e]) cudaEventDestroy(st.ev[e]);
+  for (int e = 0; e < 2; ++e)
+    if (st.ev32[e]) cudaEventDestroy(st.ev32[e]);
   st = SolveState{};
   if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
   st.t_start = now_s();
@@ -420,6 +422,8 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   for (double *p : {X, Y, W, T0, T1, L}) launch_zero<double>(p, (int64_t)big, s);
   for (int e = 0; e < 4; ++e)
     if (!st.ev[e]) PFE_CUDA_TRY(ctx, cudaEventCreate(&st.ev[e]));
+  for (int e = 0; e < 2; ++e)
+    if (!st.ev32[e]) PFE_CUDA_TRY(ctx, cudaEventCreate(&st.ev32[e]));
   // start block (stream 0 of the seeded Philox normals) and its orthonormalisation
   launch_fill_normal<double>(ctx->p_seed, 0u, n, q, 0, st.X, ld, s);
   PFE_TRY(check_launch(ctx, "start block"));
@@ -430,28 +434,40 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   }
   st.act = q;
   st.use64 = !st.fp32;
+  st.k64 = st.fp32 ? 0 : q;
   st.hth.resize(q);
   st.hr2.resize(q);
   st.it = 0;
   return PFE_OK;
 }
 
-// Y = p(Ht) X on the active columns (the single-context path)
+// Y = p(Ht) X on the active columns (the single-context path).  In the mixed-precision mode the
+// active block is ordered [FP64 columns | FP32 columns]: pairs whose residual is already below the
+// hand-over tolerance are filtered in FP64, the others in FP32 (st.k64 columns in FP64).
 pfe_status solve_filter(pfe_ctx *ctx) {
   SolveState &st = ctx->solve;
   cudaStream_t s = ctx->stream;
   const int64_t n = ctx->n, ld = st.ld;
-  st.was64 = st.use64;
-  st.f_launch += std::max(ctx->m, 1);
-  (st.use64 ? st.f_cols64 : st.f_cols32) += (int64_t)st.act * std::max(ctx->m, 1);
-  if (st.use64) {
-    PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, st.act, ld, st.X, st.Y, st.T0, st.T1, s));
+  const int32_t m1 = std::max(ctx->m, 1);
+  const int32_t k64 = st.fp32 ? std::min(st.k64, st.act) : st.act;
+  const int32_t k32 = st.act - k64;
+  st.was64 = k32 == 0;
+  if (k64 > 0) {
+    st.f_launch += m1;
+    st.f_cols64 += (int64_t)k64 * m1;
+    PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k64, ld, st.X, st.Y, st.T0, st.T1, s));
     ++st.fp64_sweeps;
-  } else {
-    launch_convert<double, float>(n, st.act, st.X, ld, st.X32, ld, s);
-    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, st.act, ld, st.X32, st.Y32, st.B32a,
-                              st.B32b, s));
-    launch_convert<float, double>(n, st.act, st.Y32, ld, st.Y, ld, s);
+  }
+  if (k32 > 0) {
+    cudaEventRecord(st.ev32[0], s);
+    st.f_launch += m1;
+    st.f_cols32 += (int64_t)k32 * m1;
+    launch_convert<double, float>(n, k32, st.X + k64, ld, st.X32 + k64, ld, s);
+    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, k32, ld, st.X32 + k64, st.Y32 + k64,
+                              st.B32a + k64, st.B32b + k64, s));
+    launch_convert<float, double>(n, k32, st.Y32 + k64, ld, st.Y + k64, ld, s);
+    cudaEventRecord(st.ev32[1], s);
+    st.timed32 = true;
   }
   st.matvecs += (int64_t)st.act * ctx->m;
   return PFE_OK;
@@ -507,7 +523,11 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
   if (st.timed_filter) {
     cudaEventElapsedTime(&ms, st.ev[0], st.ev[1]);
     st.t_filter += ms * 1e-3;
-    if (!st.was64) st.t_filter32 += ms * 1e-3;
+  }
+  if (st.timed32) {
+    cudaEventElapsedTime(&ms, st.ev32[0], st.ev32[1]);
+    st.t_filter32 += ms * 1e-3;
+    st.timed32 = false;
   }
   cudaEventElapsedTime(&ms, st.ev[1], st.ev[2]);
   st.t_orth += ms * 1e-3;
@@ -520,7 +540,6 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
   // bound then places a not yet locked eigenvalue in the interval.  Other unconverged Ritz values
   // in [a, b] can be mixtures of eigenvectors from both sides and never converge.
   std::vector<double> rr(act);
-  double worst_inside = 0.0;
   int count_in = 0, unconv_in = 0;
   for (double lv : st.lockLam)
     if (lv >= ctx->a && lv <= ctx->b) ++count_in;
@@ -530,41 +549,52 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
       return pfe_fail(ctx, PFE_E_BREAKDOWN, "non-finite Ritz value or residual");
     if (st.hth[j] > lmax * (1.0 + 1e-12)) return pfe_fail(ctx, PFE_E_BOUND, "a Ritz value exceeds the lambda_max bound");
     const double rabs = rr[j] * lmax;
-    if (st.hth[j] >= ctx->a && st.hth[j] <= ctx->b && rr[j] > tol) worst_inside = std::max(worst_inside, rr[j]);
     if (rr[j] <= tol) {
       if (st.hth[j] >= ctx->a && st.hth[j] <= ctx->b) ++count_in;
     } else if (st.hth[j] - rabs >= ctx->a && st.hth[j] + rabs <= ctx->b) {
       ++unconv_in;
     }
   }
-  // ---- lock converged pairs and compact the active block
-  std::vector<int32_t> lock_cols, keep_cols;
+  // ---- lock converged pairs and compact the active block.  Mixed precision: the kept pairs are
+  // ordered [residual <= hand-over tolerance (FP64 filter) | the rest (FP32 filter)], the FP64
+  // group padded to a multiple of 4 columns so that the FP32 group starts 16-byte aligned.
+  std::vector<int32_t> lock_cols, keep_cols, keep32;
   for (int32_t j = 0; j < act; ++j) {
     if (rr[j] <= tol && st.nl + (int32_t)lock_cols.size() < q) lock_cols.push_back(j);
+    else if (st.fp32 && rr[j] > ctx->p_refine_tol) keep32.push_back(j);
     else keep_cols.push_back(j);
   }
-  if (!lock_cols.empty()) {
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, lock_cols.data(), sizeof(int32_t) * lock_cols.size(),
-                                      cudaMemcpyHostToDevice, s));
-    launch_gather_cols(n, (int32_t)lock_cols.size(), st.X, ld, st.L + st.nl, ld, st.idx, s);
-    for (int32_t j : lock_cols) {
-      st.lockLam.push_back(st.hth[j]);
-      st.lockRes.push_back(rr[j]);
+  if (st.fp32) {
+    while (keep_cols.size() % 4 != 0 && !keep32.empty()) {
+      keep_cols.push_back(keep32.front());
+      keep32.erase(keep32.begin());
     }
-    st.nl += (int32_t)lock_cols.size();
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, keep_cols.data(), sizeof(int32_t) * std::max<size_t>(keep_cols.size(), 1),
-                                      cudaMemcpyHostToDevice, s));
-    launch_gather_cols(n, (int32_t)keep_cols.size(), st.X, ld, st.Y, ld, st.idx, s);
-    std::swap(st.X, st.Y);
+    st.k64 = (int32_t)keep_cols.size();
+    keep_cols.insert(keep_cols.end(), keep32.begin(), keep32.end());
+  }
+  const bool reorder = st.fp32 && !keep32.empty();
+  if (!lock_cols.empty() || reorder) {
+    if (!lock_cols.empty()) {
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, lock_cols.data(), sizeof(int32_t) * lock_cols.size(),
+                                        cudaMemcpyHostToDevice, s));
+      launch_gather_cols(n, (int32_t)lock_cols.size(), st.X, ld, st.L + st.nl, ld, st.idx, s);
+      for (int32_t j : lock_cols) {
+        st.lockLam.push_back(st.hth[j]);
+        st.lockRes.push_back(rr[j]);
+      }
+      st.nl += (int32_t)lock_cols.size();
+      PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // st.idx is reused below
+    }
+    if (!keep_cols.empty()) {
+      PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.idx, keep_cols.data(), sizeof(int32_t) * keep_cols.size(),
+                                        cudaMemcpyHostToDevice, s));
+      launch_gather_cols(n, (int32_t)keep_cols.size(), st.X, ld, st.Y, ld, st.idx, s);
+      std::swap(st.X, st.Y);
+    }
     PFE_TRY(check_launch(ctx, "locking"));
     PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the host index vectors must outlive the copies
   }
   st.act = (int32_t)keep_cols.size();
-  // FP32 filter: hand over to FP64 sweeps once the unconverged interval pairs are below the
-  // refinement tolerance or stop improving (the FP32 subspace has reached its accuracy floor)
-  if (!st.use64 && st.it >= 2 && (worst_inside < ctx->p_refine_tol || worst_inside > 0.5 * st.prev_worst))
-    st.use64 = true;
-  st.prev_worst = worst_inside;
   if ((unconv_in == 0 && count_in == st.prev_count && st.it >= 2) || st.act == 0) {
     st.result = (count_in >= q) ? PFE_E_CAPACITY : PFE_OK;
     st.done = true;
@@ -619,6 +649,11 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
     if (st.ev[e]) {
       cudaEventDestroy(st.ev[e]);
       st.ev[e] = nullptr;
+    }
+  for (int e = 0; e < 2; ++e)
+    if (st.ev32[e]) {
+      cudaEventDestroy(st.ev32[e]);
+      st.ev32[e] = nullptr;
     }
   if (n_found) *n_found = ctx->n_found;
   if (st.result == PFE_E_CAPACITY) return pfe_fail(ctx, st.result, "every Ritz vector lies in [a, b]: raise PFE_P_WIDTH");
@@ -978,6 +1013,8 @@ void pfe_destroy(pfe_ctx *ctx) {
   for (DBuf *b : bufs) dbuf_free(*b);
   for (int e = 0; e < 4; ++e)
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
+  for (int e = 0; e < 2; ++e)
+    if (ctx->solve.ev32[e]) cudaEventDestroy(ctx->solve.ev32[e]);
   if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   delete ctx;

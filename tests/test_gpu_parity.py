@@ -234,7 +234,7 @@ def test_solve_config_n1000_degree40():
 
 def test_solve_mixed_precision_matches_fp64_accuracy():
     st = _solve_and_check(glassgen.generate(300, 5), 0.05, 0.12, precision=1)
-    assert st["fp64_sweeps"] < st["iterations"]
+    assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] > 0  # both precisions were used
 
 
 def test_solve_capacity_error():
