@@ -35,10 +35,14 @@ WORKLOADS = {
     "glass-n100k-fp64": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=0),
     "glass-n100k-mixed": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=1),
     "glass-n1k-fp64": dict(N=1_000, seed=0, lo=0.02, hi=0.05, precision=0),
+    "glass-n20k-fp64": dict(N=20_000, seed=1, lo=0.02, hi=0.0214, precision=0),
 }
 DEFAULT = "glass-n100k-fp64"
 
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
+# DRAM traffic / algorithmic bytes of the fused step, from one ncu capture per type (N = 100,000;
+# k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md, filter_step_f32_n100k.md)
+TRAFFIC_RATIO = {8: 872.490752 / 854.171476, 4: 830.966784 / 813.542884}
 
 
 def peaks():
@@ -273,9 +277,13 @@ def run_native(args, wl):
         flops = fl * last["filter_col_steps"]
         achieved = flops / secs64 / 1e12
         b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 8, 8)
+        avg_k = last["filter_col_steps"] / max(last["filter_launches"], 1)
+        bl, _ = filter_work(g.n_atoms, nnzb, int(round(avg_k)), 8, 8)
         roof = {"bound": "alu", "kernel": "k_bsr_step<double> (fused Chebyshev step)", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
+                "traffic": TRAFFIC_RATIO[8] * bl, "traffic_note": "bytes per average launch: algorithmic x the "
+                "ncu-measured DRAM/algorithmic ratio of the k = 64 capture",
+                "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
                 "filter_gbs_fp64": (b1 / last["width"]) * last["filter_col_steps"] / secs64 / 1e9,
                 "launches": last["filter_launches"]}
     else:

@@ -85,7 +85,12 @@ enum {
                                same with two 3x3 blocks in flight per iteration, 4: neighbour rows staged
                                in shared memory by cp.async four blocks ahead (16-byte lanes), 5 and 6:
                                0 and 1 compiled for five resident CTAs per SM */
-  PFE_P_STEP_SHAPE_F32 = 20  /* PROCESS-WIDE: the same for the FP32 filter step */
+  PFE_P_STEP_SHAPE_F32 = 20, /* PROCESS-WIDE: the same for the FP32 filter step */
+  PFE_P_METHOD = 21,        /* 0: filtered subspace iteration (Alg. 4, default); 1: thick-restart block
+                               Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),
+                               FP64 only */
+  PFE_P_BLOCK = 22,         /* block size of METHOD 1 (default 64) */
+  PFE_P_BASIS_FACTOR = 23   /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 3, Sec. 3) */
 };
 
 /* ---------------------------------------------------------------------------------------
@@ -137,7 +142,8 @@ pfe_status pfe_estimate(pfe_ctx *ctx, double *lambda_max, double *count_est);
 pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs, double *c, double *d);
 
 /* Alg. 3, solve step: compute all eigenpairs with lambda in [a, b] by filtered subspace iteration
- * (Alg. 4 with Rayleigh-Ritz on H every iteration, CholQR2 orthonormalisation, locking).
+ * (Alg. 4 with Rayleigh-Ritz on H every iteration, CholQR2 orthonormalisation, locking), or with
+ * PFE_P_METHOD = 1 by thick-restart block Lanczos on p(Ht) followed by Rayleigh-Ritz with H.
  * *n_found receives their number.  Results stay in the context.
  * PFE_E_CAPACITY: the subspace was too narrow to certify completeness (raise PFE_P_WIDTH);
  * PFE_E_NOCONV: the iteration limit was hit (partial results are kept). */
@@ -176,6 +182,8 @@ typedef struct {
   int64_t filter_col_steps_f32;/* the same for the FP32 filter */
   double seconds_filter_f32;   /* part of seconds_filter spent in FP32 filter sweeps */
   int64_t batch_replays;       /* pfe_solve_batch: replays of the captured batched-filter graph */
+  int32_t restarts;            /* METHOD 1: thick restarts */
+  int32_t basis;               /* METHOD 1: maximal basis size */
 } pfe_stats;
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 

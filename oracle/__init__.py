@@ -78,6 +78,8 @@ def _load():
         _sig(lib, "or_si_solve", ctypes.c_int,
              [_P, _D, _D, _D, _D, _P, _I32, _I32, _P, _D, _I32, _I32, _P, _P, _P, _P, _P, _P])
         _sig(lib, "or_si_alg4_diag", _I32, [_I64, _P, _I32, _I32, _I32, _D, _P, _I32])
+        _sig(lib, "or_bks_solve", ctypes.c_int,
+             [_P, _D, _D, _D, _D, _P, _I32, _I32, _I32, _I32, _P, _D, _D, _I32, _I32, _P, _P, _P, _P, _P, _P])
         _sig(lib, "or_filter_adjoint", ctypes.c_int,
              [_P, _D, _D, _P, _I32, _I32, _P, _I64, _P, _I64, _P, _I64, _P])
         _sig(lib, "or_chain_springs", None, [_P, _I32, _I64, _P, _P, _P, _P, _P, _P, _P, _P])
@@ -308,6 +310,25 @@ def si_solve(H: CSR, a, b, lmin, lmax, coef, q, X0, tol=1e-8, max_iter=100, cap=
                              ctypes.byref(mv))
     if st < 0:
         raise ValueError(f"si_solve: bad arguments ({st})")
+    k = min(nf.value, cap)
+    return SIResult(st, lam[:k].copy(), vec[:, :k].copy(), res[:k].copy(), it.value, mv.value)
+
+
+def bks_solve(H: CSR, a, b, lmin, lmax, coef, bs, maxbasis, keep_min, X0, theta_cut, tol=1e-8, max_restarts=50,
+              cap=None) -> SIResult:
+    """Thick-restart block Lanczos on p(Ht), then Rayleigh-Ritz with H (see oracle.c)."""
+    coef = _f64(coef)
+    X0 = _fortran(X0.reshape(H.n, bs))
+    cap = maxbasis if cap is None else cap
+    lam = np.zeros(cap)
+    vec = np.zeros((H.n, cap), order="F")
+    res = np.zeros(cap)
+    nf, it, mv = _I32(), _I32(), _I64()
+    st = _load().or_bks_solve(H.handle, a, b, lmin, lmax, _ptr(coef), coef.shape[0] - 1, bs, maxbasis, keep_min,
+                              _ptr(X0), theta_cut, tol, max_restarts, cap, ctypes.byref(nf), _ptr(lam), _ptr(vec),
+                              _ptr(res), ctypes.byref(it), ctypes.byref(mv))
+    if st < 0:
+        raise ValueError(f"bks_solve: bad arguments ({st})")
     k = min(nf.value, cap)
     return SIResult(st, lam[:k].copy(), vec[:, :k].copy(), res[:k].copy(), it.value, mv.value)
 

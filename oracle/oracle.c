@@ -1046,3 +1046,206 @@ void or_chain_springs(const or_csr *H, int32_t N, int64_t nb, const int32_t *bi,
     mbar[i] = -off / (2.0 * mass[i]) - dia / mass[i];
   }
 }
+
+/* ======================================================================================
+ * Thick-restart block Lanczos on the filter operator Op = p(Ht) (Sec. 2.5 and Sec. 3: the block
+ * Krylov-Schur / thick-restart Lanczos eigensolver applied to the matrix polynomial), followed by
+ * Rayleigh-Ritz with H on the converged wanted Op-eigenvectors (Sec. 2.5: "the correct
+ * eigenvalue-eigenvector relations can be found by a Rayleigh-Ritz procedure applied to H").
+ *
+ * Krylov basis V (orthonormal, block size bs) and OV = Op V for its first nv columns.
+ *   expand:  OV_j = Op V_j; W = OV_j - V (V^T OV_j) (twice); V_{j+1} = QR(W) (twice against V)
+ *   restart: T = V^T OV (nv x nv), T = S Theta S^T (Jacobi), Y = V S, OY = OV S,
+ *            r_i = ||OY_i - theta_i Y_i||; keep the `keep` largest Ritz pairs as the new basis and
+ *            the last block V_{j+1} (orthogonal to all of V) as the continuation block.
+ *   stop:    every Ritz pair with theta >= theta_cut has r_i <= tol_op * max|theta|, at least one
+ *            block of Ritz values lies below theta_cut (the wanted set is not truncated), and the
+ *            number of wanted Ritz pairs equals that of the previous restart.
+ * Final:    A = Yw^T H Yw for the wanted converged Yw, A = Q Lambda Q^T, U = Yw Q; pairs with lambda
+ *            in [a, b] and residual ||H u - lambda u|| / lmax <= tol are returned, ascending.  If a
+ *            returned residual exceeds tol, tol_op is divided by 100 and the iteration continues.
+ * Returns 0 on success, 1 iteration limit, 2 capacity exceeded, <0 bad input.
+ * ==================================================================================== */
+static void or_cgs2(int64_t n, const double *V, int32_t nv, double *W, int32_t k, double *h) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int32_t c = 0; c < k; ++c) {
+      double *w = W + (int64_t)c * n;
+      for (int32_t l = 0; l < nv; ++l) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; ++i) s += V[(int64_t)l * n + i] * w[i];
+        h[l] = s;
+      }
+      for (int32_t l = 0; l < nv; ++l)
+        for (int64_t i = 0; i < n; ++i) w[i] -= h[l] * V[(int64_t)l * n + i];
+    }
+}
+
+int or_bks_solve(const or_csr *H, double a, double b, double lmin, double lmax, const double *coef, int32_t m,
+                 int32_t bs, int32_t maxbasis, int32_t keep_min, const double *X0, double theta_cut, double tol,
+                 int32_t max_restarts, int32_t cap, int32_t *n_found, double *lam_out, double *vec_out,
+                 double *res_out, int32_t *restarts_out, int64_t *matvecs_out) {
+  const int64_t n = H->n;
+  if (bs < 1 || maxbasis < 3 * bs || maxbasis + bs > n) return -1;
+  const double c = 0.5 * (lmax + lmin), d = 0.5 * (lmax - lmin);
+  double *V = (double *)calloc((size_t)n * (size_t)(maxbasis + bs), sizeof(double));
+  double *OV = (double *)calloc((size_t)n * (size_t)maxbasis, sizeof(double));
+  double *Y = (double *)malloc(sizeof(double) * (size_t)n * maxbasis);
+  double *OY = (double *)malloc(sizeof(double) * (size_t)n * maxbasis);
+  double *T = (double *)malloc(sizeof(double) * (size_t)maxbasis * maxbasis);
+  double *S = (double *)malloc(sizeof(double) * (size_t)maxbasis * maxbasis);
+  double *th = (double *)malloc(sizeof(double) * (size_t)maxbasis);
+  double *rr = (double *)malloc(sizeof(double) * (size_t)maxbasis);
+  double *h = (double *)malloc(sizeof(double) * (size_t)(maxbasis + bs));
+  int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * (size_t)maxbasis);
+  if (!V || !OV || !Y || !OY || !T || !S || !th || !rr || !h || !ord) {
+    free(V); free(OV); free(Y); free(OY); free(T); free(S); free(th); free(rr); free(h); free(ord);
+    return -4;
+  }
+  memcpy(V, X0, sizeof(double) * (size_t)n * bs);
+  or_householder_qr(n, bs, V, n, NULL);
+  int32_t nv = 0, restarts = 0, status = 1, nf = 0, prev_nwant = -1;
+  int64_t mv = 0;
+  double tol_op = 1e-10;
+  for (;;) {
+    /* expand the basis (with Op applied) while another block fits into maxbasis columns */
+    while (nv + bs <= maxbasis) {
+      double *Vj = V + (int64_t)nv * n, *OVj = OV + (int64_t)nv * n;
+      mv += or_cheb_filter(H, c, d, coef, m, bs, Vj, n, OVj, n);
+      double *Wn = V + (int64_t)(nv + bs) * n;
+      memcpy(Wn, OVj, sizeof(double) * (size_t)n * bs);
+      or_cgs2(n, V, nv + bs, Wn, bs, h);
+      or_householder_qr(n, bs, Wn, n, NULL);
+      or_cgs2(n, V, nv + bs, Wn, bs, h);
+      or_householder_qr(n, bs, Wn, n, NULL);
+      nv += bs;
+    }
+    /* Rayleigh-Ritz of Op on span(V) */
+    for (int32_t j = 0; j < nv; ++j)
+      for (int32_t i = 0; i < nv; ++i) {
+        double s = 0.0;
+        for (int64_t r = 0; r < n; ++r) s += V[(int64_t)i * n + r] * OV[(int64_t)j * n + r];
+        T[(int64_t)j * nv + i] = s;
+      }
+    for (int32_t j = 0; j < nv; ++j)
+      for (int32_t i = 0; i < j; ++i) {
+        double s = 0.5 * (T[(int64_t)j * nv + i] + T[(int64_t)i * nv + j]);
+        T[(int64_t)j * nv + i] = s;
+        T[(int64_t)i * nv + j] = s;
+      }
+    or_jacobi_eig(nv, T, th, S);
+    for (int32_t i = 0; i < nv; ++i) ord[i] = nv - 1 - i; /* descending theta */
+    for (int32_t jj = 0; jj < nv; ++jj) {
+      int32_t j = ord[jj];
+      for (int64_t r = 0; r < n; ++r) {
+        double sy = 0.0, so = 0.0;
+        for (int32_t i = 0; i < nv; ++i) {
+          double sij = S[(int64_t)j * nv + i];
+          sy += V[(int64_t)i * n + r] * sij;
+          so += OV[(int64_t)i * n + r] * sij;
+        }
+        Y[(int64_t)jj * n + r] = sy;
+        OY[(int64_t)jj * n + r] = so;
+      }
+      double s2 = 0.0;
+      for (int64_t r = 0; r < n; ++r) {
+        double e = OY[(int64_t)jj * n + r] - th[j] * Y[(int64_t)jj * n + r];
+        s2 += e * e;
+      }
+      rr[jj] = sqrt(s2);
+    }
+    double thmax = fabs(th[ord[0]]);
+    int32_t nwant = 0, nconv = 0;
+    for (int32_t jj = 0; jj < nv; ++jj)
+      if (th[ord[jj]] >= theta_cut) {
+        ++nwant;
+        if (rr[jj] <= tol_op * thmax) ++nconv;
+      }
+    int done = (nwant == nconv) && (nwant <= nv - bs) && (nwant == prev_nwant);
+    prev_nwant = nwant;
+    if (done) {
+      /* Rayleigh-Ritz with H on the wanted Op-eigenvectors (the first nwant columns of Y) */
+      int32_t k = nwant;
+      double *HY = OY; /* reuse */
+      or_spmm(H, k, Y, n, HY, n);
+      mv += k;
+      double *A = T, *Q = S;
+      for (int32_t j = 0; j < k; ++j)
+        for (int32_t i = 0; i < k; ++i) {
+          double s = 0.0;
+          for (int64_t r = 0; r < n; ++r) s += Y[(int64_t)i * n + r] * HY[(int64_t)j * n + r];
+          A[(int64_t)j * k + i] = s;
+        }
+      for (int32_t j = 0; j < k; ++j)
+        for (int32_t i = 0; i < j; ++i) {
+          double s = 0.5 * (A[(int64_t)j * k + i] + A[(int64_t)i * k + j]);
+          A[(int64_t)j * k + i] = s;
+          A[(int64_t)i * k + j] = s;
+        }
+      double *ev = rr; /* k <= maxbasis */
+      or_jacobi_eig(k, A, ev, Q);
+      double *U = OV; /* n x k */
+      for (int32_t j = 0; j < k; ++j)
+        for (int64_t r = 0; r < n; ++r) {
+          double s = 0.0;
+          for (int32_t i = 0; i < k; ++i) s += Y[(int64_t)i * n + r] * Q[(int64_t)j * k + i];
+          U[(int64_t)j * n + r] = s;
+        }
+      double *w = (double *)malloc(sizeof(double) * (size_t)n);
+      int bad = 0;
+      nf = 0;
+      for (int32_t j = 0; j < k; ++j) {
+        if (ev[j] < a || ev[j] > b) continue;
+        or_spmm(H, 1, U + (int64_t)j * n, n, w, n);
+        double s2 = 0.0;
+        for (int64_t r = 0; r < n; ++r) {
+          double e = w[r] - ev[j] * U[(int64_t)j * n + r];
+          s2 += e * e;
+        }
+        double res = sqrt(s2) / lmax;
+        if (res > tol) bad = 1;
+        if (nf < cap) {
+          lam_out[nf] = ev[j];
+          if (res_out) res_out[nf] = res;
+          if (vec_out) memcpy(vec_out + (int64_t)nf * n, U + (int64_t)j * n, sizeof(double) * (size_t)n);
+        }
+        ++nf;
+      }
+      free(w);
+      if (!bad || tol_op < 1e-15) {
+        status = (nf > cap) ? 2 : (bad ? 1 : 0);
+        break;
+      }
+      tol_op *= 1e-2; /* the Op-residuals were not small enough for the H-residuals: iterate on */
+      /* the basis was overwritten by the final Rayleigh-Ritz: restore it from Y (kept below) */
+    }
+    if (++restarts > max_restarts) {
+      status = 1;
+      nf = 0;
+      break;
+    }
+    /* thick restart: keep the `keep` largest Ritz pairs plus the continuation block */
+    int32_t keep = nwant + bs;
+    if (keep < keep_min) keep = keep_min;
+    if (keep > nv - bs) keep = nv - bs;
+    if (done) {
+      /* OY was reused for H Y: recompute Op Y for the kept columns from the stored basis is not
+         possible, so rebuild OY = OV_old S is lost; fall back to re-applying Op to the kept block */
+      memcpy(V, Y, sizeof(double) * (size_t)n * keep);
+      mv += or_cheb_filter(H, c, d, coef, m, keep, V, n, OV, n);
+    } else {
+      memcpy(V, Y, sizeof(double) * (size_t)n * keep);
+      memcpy(OV, OY, sizeof(double) * (size_t)n * keep);
+    }
+    /* continuation block: the last Krylov block, orthogonal to the old basis */
+    memmove(V + (int64_t)keep * n, V + (int64_t)nv * n, sizeof(double) * (size_t)n * bs);
+    or_cgs2(n, V, keep, V + (int64_t)keep * n, bs, h);
+    or_householder_qr(n, bs, V + (int64_t)keep * n, n, NULL);
+    nv = keep;
+  }
+  *n_found = nf;
+  if (restarts_out) *restarts_out = restarts;
+  if (matvecs_out) *matvecs_out = mv;
+  /* ascending order of the returned pairs (Jacobi already returns ascending eigenvalues) */
+  free(V); free(OV); free(Y); free(OY); free(T); free(S); free(th); free(rr); free(h); free(ord);
+  return status;
+}

@@ -33,6 +33,7 @@ PFE_P_WIDTH_FACTOR, PFE_P_TOL, PFE_P_PRECISION, PFE_P_MAX_ITERS, PFE_P_SEED = 6,
 PFE_P_LAMBDA_MAX, PFE_P_LAMBDA_MIN, PFE_P_COUNT_M, PFE_P_COUNT_DEGREE = 11, 12, 13, 14
 PFE_P_LANCZOS_STEPS, PFE_P_COUNT_DAMPING, PFE_P_MIN_WIDTH, PFE_P_REFINE_TOL = 15, 16, 17, 18
 PFE_P_STEP_SHAPE_F64, PFE_P_STEP_SHAPE_F32 = 19, 20
+PFE_P_METHOD, PFE_P_BLOCK, PFE_P_BASIS_FACTOR = 21, 22, 23
 
 # every entry point declared in include/pfe.h
 EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", "pfe_set_param",
@@ -56,7 +57,8 @@ class PfeStats(ctypes.Structure):
                 ("fp64_sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("window_estimate", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
                 ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
-                ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64)]
+                ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64),
+                ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

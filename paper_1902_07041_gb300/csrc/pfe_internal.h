@@ -212,6 +212,9 @@ struct pfe_ctx {
   int p_count_damping = 0;
   int32_t p_min_width = 16;
   double p_refine_tol = 1e-4;
+  int p_method = 0;
+  int32_t p_block = 64;
+  double p_basis_factor = 3.0;
 
   // state
   bool has_interval = false;
@@ -236,13 +239,25 @@ struct pfe_ctx {
 
   // workspaces
   pfe::DBuf w_X, w_Y, w_W, w_T0, w_T1, w_T2, w_small, w_small2, w_red, w_idx, w_cs_work, w_info, w_f32a, w_f32b,
-      w_f32c, w_f32d, w_ckpt, w_rr, w_gram;
+      w_f32c, w_f32d, w_ckpt, w_rr, w_gram, w_bks[5];
   int64_t launch_base = 0;  // process-wide launch counter when the context was created
   SolveState solve;
   pfe::DBuf dcoef;            // filter coefficients on the device (batched solves)
   int tuned_cpl = 0, tuned_blocks = 0;  // autotuned batched-filter shape of the last batch
   std::string err;
 };
+
+// the thick-restart block Lanczos solve (bks.cu); uses the pieces below from solver.cu
+pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found);
+namespace pfe {
+pfe_status solver_ensure_filter(pfe_ctx *ctx);
+pfe_status solver_ensure_hs(pfe_ctx *ctx, bool need32);
+pfe_status solver_count(pfe_ctx *ctx);
+pfe_status solver_window(pfe_ctx *ctx, double *out);
+pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result);
+pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1);
+double solver_now();
+}  // namespace pfe
 
 // status helpers used across the host sources
 pfe_status pfe_fail(pfe_ctx *ctx, pfe_status st, const std::string &msg);

@@ -823,6 +823,20 @@ pfe_status batch_filter(pfe_ctx *c0, pfe_ctx **ctxs, int32_t ns, const std::vect
 
 }  // namespace
 
+namespace pfe {
+pfe_status solver_ensure_filter(pfe_ctx *ctx) { return ensure_filter(ctx); }
+pfe_status solver_ensure_hs(pfe_ctx *ctx, bool need32) { return ensure_hs(ctx, need32); }
+pfe_status solver_count(pfe_ctx *ctx) { return count_estimate(ctx); }
+pfe_status solver_window(pfe_ctx *ctx, double *out) { return window_estimate(ctx, out); }
+pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result) {
+  return cholqr2(ctx, Y, tmp, k, ld, result);
+}
+pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1) {
+  return run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k, ld, X, Y, b0, b1, ctx->stream);
+}
+double solver_now() { return now_s(); }
+}  // namespace pfe
+
 // =====================================================================================
 // C ABI
 // =====================================================================================
@@ -1009,7 +1023,8 @@ void pfe_destroy(pfe_ctx *ctx) {
   DBuf *bufs[] = {&ctx->rp, &ctx->ci, &ctx->H, &ctx->mass, &ctx->Hs64, &ctx->Hs32, &ctx->L, &ctx->w_X, &ctx->w_Y,
                   &ctx->w_W, &ctx->w_T0, &ctx->w_T1, &ctx->w_T2, &ctx->w_small, &ctx->w_small2, &ctx->w_red,
                   &ctx->w_idx, &ctx->w_cs_work, &ctx->w_info, &ctx->w_f32a, &ctx->w_f32b, &ctx->w_f32c,
-                  &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram};
+                  &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram,
+                  &ctx->w_bks[0], &ctx->w_bks[1], &ctx->w_bks[2], &ctx->w_bks[3], &ctx->w_bks[4]};
   for (DBuf *b : bufs) dbuf_free(*b);
   for (int e = 0; e < 4; ++e)
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
@@ -1110,6 +1125,18 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!(v > 0)) return pfe_fail(ctx, PFE_E_ARG, "REFINE_TOL must be > 0");
       ctx->p_refine_tol = v;
       break;
+    case PFE_P_METHOD:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "METHOD must be 0 or 1");
+      ctx->p_method = (int)v;
+      break;
+    case PFE_P_BLOCK:
+      if (!int_ok(1) || v > 4096) return pfe_fail(ctx, PFE_E_ARG, "BLOCK must be an integer in [1, 4096]");
+      ctx->p_block = (int32_t)v;
+      break;
+    case PFE_P_BASIS_FACTOR:
+      if (!(v >= 2.0)) return pfe_fail(ctx, PFE_E_ARG, "BASIS_FACTOR must be >= 2");
+      ctx->p_basis_factor = v;
+      break;
     case PFE_P_STEP_SHAPE_F64:
     case PFE_P_STEP_SHAPE_F32:
       if (!(v == -1 || (v >= 0 && v <= 6 && v == std::floor(v))))
@@ -1143,6 +1170,9 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_COUNT_DAMPING: *v = ctx->p_count_damping; break;
     case PFE_P_MIN_WIDTH: *v = ctx->p_min_width; break;
     case PFE_P_REFINE_TOL: *v = ctx->p_refine_tol; break;
+    case PFE_P_METHOD: *v = ctx->p_method; break;
+    case PFE_P_BLOCK: *v = ctx->p_block; break;
+    case PFE_P_BASIS_FACTOR: *v = ctx->p_basis_factor; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;
@@ -1193,6 +1223,7 @@ pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs,
 pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
   if (!ctx) return PFE_E_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  if (ctx->p_method == 1) return bks_solve(ctx, n_found);
   SolveState &st = ctx->solve;
   PFE_TRY(solve_setup(ctx));
   while (!st.done) {

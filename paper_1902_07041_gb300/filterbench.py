@@ -26,7 +26,8 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--degree", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--shape", type=int, default=-1, help="kernel shape 0..3, -1 = autotuned")
+    ap.add_argument("--shape", type=int, default=-1, help="kernel shape 0..6, -1 = autotuned")
+    ap.add_argument("--adjoint", action="store_true", help="time pfe_filter_adjoint (FP64) at this degree instead")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
@@ -44,6 +45,25 @@ def main():
         nnzb = ci.size
         step_bytes = -(-a.k // kt) * (nnzb * (9 * s + 4) + 4 * (g.n_atoms + 1)) + 5 * g.n * a.k * s
         step_flops = 18 * nnzb * a.k + 6 * g.n * a.k
+        if a.adjoint:
+            coef = np.ones(a.degree + 1) / (a.degree + 1)
+            Xb = torch.empty_like(X)
+            vb = torch.empty(9 * ci.size, device="cuda", dtype=torch.float64)
+            pfe.pfe_filter_adjoint(ctx, a.degree, coef, a.k, X, g.n, Y, g.n, Xb, g.n, vb)
+            torch.cuda.synchronize()
+            for _ in range(a.reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                pfe.pfe_filter_adjoint(ctx, a.degree, coef, a.k, X, g.n, Y, g.n, Xb, g.n, vb)
+                e1.record()
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                # forward (m steps), segment recomputation (~m steps), reverse (m steps) and the
+                # outer products (9 FMA per block and column per step)
+                flops = 3 * a.degree * step_flops + a.degree * 18 * nnzb * a.k
+                print(json.dumps({"n_atoms": g.n_atoms, "k": a.k, "degree": a.degree, "adjoint_s": t,
+                                  "alg_gflops": flops / t / 1e9}), flush=True)
+            return
         times = {}
         for m in (1, a.degree + 1):
             coef = np.ones(m + 1) / (m + 1)

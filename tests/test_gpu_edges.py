@@ -1,0 +1,125 @@
+"""Edge cases of the filtered subspace iteration on the GPU, through the C ABI, against the oracle
+and closed forms: an interval without eigenvalues, the zero (translation) modes at lambda = 0, the
+top of the spectrum, exactly degenerate eigenvalues, and the synthetic diagonal problem of the
+paper's Sec. 4.1 (test case 1, equally distributed eigenvalues) with known eigenpairs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import glassgen  # noqa: E402
+import oracle  # noqa: E402
+import paper_1902_07041_gb300 as pfe  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    pfe.load()
+
+
+def _solve(rp, ci, vals, n_atoms, masses, lo, hi, absolute=False, **params):
+    ctx = pfe.pfe_create(n_atoms, rp, ci, vals, masses)
+    try:
+        for k, v in params.items():
+            pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + k), v)
+        lmax, _ = pfe.pfe_estimate(ctx)
+        a, b = (lo, hi) if absolute else (lo * lmax, hi * lmax)
+        pfe.pfe_set_interval(ctx, a, b)
+        nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
+        lam, V, res = pfe.pfe_get_eigenpairs(ctx, 3 * n_atoms, nf) if nf else (np.zeros(0), None, None)
+        return st, nf, lam, V, lmax, a, b
+    finally:
+        pfe.pfe_destroy(ctx)
+
+
+def _glass(n, seed):
+    g = glassgen.generate(n, seed)
+    return g, pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+
+
+def test_interval_without_eigenvalues():
+    g, (rp, ci, vals) = _glass(200, 31)
+    w = np.linalg.eigvalsh(oracle.csr_from_springs(g).dense())
+    gaps = np.diff(w)
+    i = int(np.argmax(gaps[len(w) // 4: len(w) // 2])) + len(w) // 4  # a wide gap in the lower spectrum
+    a, b = w[i] + 0.3 * gaps[i], w[i] + 0.7 * gaps[i]
+    st, nf, lam, _, _, _, _ = _solve(rp, ci, vals, g.n_atoms, g.mass, a, b, absolute=True)
+    assert st == pfe.PFE_OK and nf == 0
+
+
+def test_zero_modes_at_the_bottom_of_the_spectrum():
+    """[0, b] starts at the three translation modes sqrt(m_i) e_x (lambda = 0).  Computed in FP64 they
+    sit within rounding of the edge a = 0 and may fall on either side of it (boundary-ambiguous);
+    every other eigenvalue of [0, b] must be found, and whatever is found near 0 must lie in the
+    translation space."""
+    g, (rp, ci, vals) = _glass(150, 32)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, g.n_atoms, g.mass, 0.0, 0.04)
+    H = oracle.csr_from_springs(g)
+    w, _, _ = oracle.exact_interval(H, 1e-9 * lmax, b)
+    assert st == pfe.PFE_OK
+    nz = lam > 1e-9 * lmax
+    assert int(nz.sum()) == w.size and nf - int(nz.sum()) <= 3
+    assert np.allclose(lam[nz], w, rtol=1e-10, atol=0)
+    T = np.zeros((H.n, 3))
+    for ax in range(3):
+        T[ax::3, ax] = np.sqrt(g.mass)
+    T /= np.linalg.norm(T, axis=0)
+    Z = V[:, ~nz]
+    if Z.shape[1]:
+        assert np.allclose(np.linalg.norm(T.T @ Z, axis=0), 1.0, atol=1e-8)  # inside the translation space
+
+
+def test_top_of_the_spectrum():
+    g, (rp, ci, vals) = _glass(150, 33)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, g.n_atoms, g.mass, 0.85, 1.0)
+    H = oracle.csr_from_springs(g)
+    w, _, _ = oracle.exact_interval(H, a, b)
+    assert st == pfe.PFE_OK and nf == w.size and nf > 0
+    assert np.allclose(lam, w, rtol=1e-10, atol=0)
+
+
+def _block_diagonal(diag_values):
+    """BSR of a block-diagonal matrix with 3x3 diagonal blocks diag(d_3i, d_3i+1, d_3i+2)."""
+    n = diag_values.size
+    N = n // 3
+    rp = np.arange(N + 1, dtype=np.int32)
+    ci = np.arange(N, dtype=np.int32)
+    vals = np.zeros(9 * N)
+    for i in range(N):
+        vals[9 * i + 0], vals[9 * i + 4], vals[9 * i + 8] = diag_values[3 * i:3 * i + 3]
+    return rp, ci, vals
+
+
+def test_exactly_degenerate_eigenvalues():
+    """Eigenvalues of multiplicity 3 (each diagonal value repeated in a whole block): the count is
+    exact and each eigenvalue's computed space is the coordinate space of its value."""
+    base = np.repeat(np.linspace(0.0, 1.0, 400), 3)  # each value 3 times, blocks identical multiples
+    rp, ci, vals = _block_diagonal(base)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, 400, None, 0.30, 0.36, absolute=True, LAMBDA_MAX=1.01)
+    sel = (base >= a) & (base <= b)
+    assert st == pfe.PFE_OK and nf == int(sel.sum())
+    assert np.allclose(lam, np.sort(base[sel]), rtol=0, atol=1e-12)
+    # the computed subspace equals the span of the selected coordinate vectors
+    assert np.allclose(np.linalg.norm(V[sel, :], axis=0), 1.0, atol=1e-10)
+
+
+def test_paper_diagonal_test_case_1():
+    """Sec. 4.1, test case 1: equally distributed eigenvalues lambda_i = -1 + (2i - 1)/n shifted by +1
+    into [0, 2] (H must be PSD here); the 50 eigenvalues of (-0.9, -0.898) + 1, eigenvectors e_i."""
+    n = 50001  # 16,667 atoms: the paper's n = 50,000 plus one eigenvalue at the top
+    lam_all = -1 + (2 * np.arange(1, 50001) - 1) / 50000.0 + 1.0
+    lam_all = np.append(lam_all, 2.0)
+    rp, ci, vals = _block_diagonal(lam_all)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, n // 3, None, 0.1, 0.102, absolute=True, LAMBDA_MAX=2.0,
+                                        EPS_FRAC=0.25)
+    sel = (lam_all >= a) & (lam_all <= b)
+    assert int(sel.sum()) == 50
+    assert st == pfe.PFE_OK and nf == 50
+    assert np.allclose(lam, lam_all[sel], rtol=0, atol=1e-12)
+    idx = np.nonzero(sel)[0]
+    assert np.allclose(np.abs(V[idx, np.arange(50)]), 1.0, atol=1e-8)

@@ -237,6 +237,17 @@ def test_solve_mixed_precision_matches_fp64_accuracy():
     assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] > 0  # both precisions were used
 
 
+@pytest.mark.parametrize("block", [16, 64])
+def test_solve_block_lanczos(block):
+    """Thick-restart block Lanczos on p(Ht) + Rayleigh-Ritz with H (PFE_P_METHOD = 1)."""
+    st = _solve_and_check(glassgen.generate(300, 5), 0.05, 0.12, METHOD=1, BLOCK=block)
+    assert st["basis"] >= 3 * block
+
+
+def test_solve_block_lanczos_n1000():
+    _solve_and_check(glassgen.generate(1000, 0), 0.02, 0.05, METHOD=1, BLOCK=32)
+
+
 def test_solve_capacity_error():
     g = glassgen.generate(300, 5)
     ctx, _ = make_ctx(g, WIDTH=8)
