@@ -84,13 +84,22 @@ enum {
                                0 warp per (atom, column chunk), 1 CTA per 8 atoms x chunk, 2 and 3: the
                                same with two 3x3 blocks in flight per iteration, 4: neighbour rows staged
                                in shared memory by cp.async four blocks ahead (16-byte lanes), 5 and 6:
-                               0 and 1 compiled for five resident CTAs per SM */
+                               0 and 1 compiled for five resident CTAs per SM; 7, 8, 9: the rank-1
+                               form (PFE_P_RANK1) as 0, 5 and 2 (shape 0 when there is none) */
   PFE_P_STEP_SHAPE_F32 = 20, /* PROCESS-WIDE: the same for the FP32 filter step */
   PFE_P_METHOD = 21,        /* 0: filtered subspace iteration (Alg. 4, default); 1: thick-restart block
                                Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),
                                FP64 only */
   PFE_P_BLOCK = 22,         /* block size of METHOD 1 (default 64) */
-  PFE_P_BASIS_FACTOR = 23   /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 3, Sec. 3) */
+  PFE_P_BASIS_FACTOR = 23,  /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 3, Sec. 3) */
+  PFE_P_BATCH_THREADS = 24, /* pfe_solve_batch, read from the first context: host threads that run the
+                               samples' set-up and dense steps concurrently, each sample on its own
+                               stream (0 = automatic: min(samples, hardware threads, 16); 1 = serial) */
+  PFE_P_RANK1 = 25          /* 1 (default): when every off-diagonal block of H is -k r r^T / sqrt(m_i m_j)
+                               (a central-force network, eqs. (1)-(2)) the filter steps use that rank-1
+                               form, 6 FMAs a block and column instead of 9; 0: always the full 3x3
+                               blocks.  pfe_get_param returns whether the form is in use (it is checked
+                               when the filter operator is first built) */
 };
 
 /* ---------------------------------------------------------------------------------------
@@ -246,7 +255,8 @@ pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeff
  * interval set; all must live on one device.  The iterations of all samples advance in lockstep:
  * the filter of every FP64 sample runs as one persistent kernel per Chebyshev step over all
  * samples' work, captured once in a CUDA graph and replayed per iteration (its column tile and
- * grid size chosen by timing the candidates on the first call); the dense steps run per sample.
+ * grid size chosen by timing the candidates on the first call); the dense steps run per sample,
+ * the samples' dense steps concurrently from PFE_P_BATCH_THREADS host threads.
  * In the stats of every sample seconds_filter is the batch's shared filter time.
  * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);

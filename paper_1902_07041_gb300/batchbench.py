@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--hi", type=float, default=0.026)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--solo", action="store_true", help="also time the samples solved one by one")
+    ap.add_argument("--threads", type=int, default=0, help="host threads for the per-sample steps (0: automatic)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     sizes = glassgen.batch_sizes(a.samples, a.seed, a.n_min, a.n_max)
@@ -43,6 +44,7 @@ def main():
         for g, (rp, ci, vals) in problems:
             ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
             pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, a.precision)
+            pfe.pfe_set_param(ctx, pfe.PFE_P_BATCH_THREADS, a.threads)
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, a.lo * lmax, a.hi * lmax)
             ctxs.append(ctx)

@@ -42,7 +42,7 @@ def _stale(srcs) -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "pfe.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -70,7 +70,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     libdir = _cuda_lib_dir(nvcc)
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + [
-        "-L", libdir, "-lcublas", "-lcusolver", "-Xlinker", f"-rpath={libdir}"]
+        "-L", libdir, "-lcublas", "-lcusolver", "-Xlinker", f"-rpath={libdir}",
+        "-Xlinker", "-z", "-Xlinker", "defs"]  # an undefined symbol fails the link, not the first load
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link of libpfe.so failed:\n{r.stderr}")

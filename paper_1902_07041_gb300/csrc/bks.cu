@@ -1,19 +1,26 @@
 // Thick-restart block Lanczos on the filter operator Op = p(Ht) (the block Krylov-Schur solver the
-// paper runs in production, Sec. 2.5 and Sec. 3), followed by Rayleigh-Ritz with H on the converged
-// wanted Op-eigenvectors ("the correct eigenvalue-eigenvector relations can be found by a
-// Rayleigh-Ritz procedure applied to H", Sec. 2.5).
+// paper runs in production, Sec. 2.5 and Sec. 3), followed by Rayleigh-Ritz with H on the wanted
+// Op-eigenvectors: the eigenvectors of Op are those of H, and a Rayleigh-Ritz step with H recovers
+// the eigenvalues (Sec. 2.5).
 //
-// Basis V (orthonormal, row-major n x ldv) and OV = Op V for its first nv columns:
-//   expand:  OV_j = Op V_j (fused filter, bs columns); W = OV_j - V (V^T OV_j), twice (DMMA);
-//            V_{j+1} = CholQR2(W), twice against V;
-//   restart: T = V^T OV (DMMA Gram), T = S Theta S^T (cuSOLVER); the `keep` largest Ritz pairs
-//            Y = V S, OY = OV S become the new basis; the last block V_{j+1} (orthogonal to all of
-//            V) continues the Krylov sequence;
-//   stop:    every Ritz pair with theta >= theta_cut has ||OY - theta Y|| <= tol_op max|theta|,
-//            at least one block of Ritz values lies below theta_cut, and the number of wanted
-//            pairs did not change since the previous restart.
-// theta_cut = sqrt(r) min(p(xi), p(eta)): below the filter's value at the interval edges and
-// above its value r min(p(xi), p(eta)) outside the margins (eq. (thresh)).
+// Basis V (orthonormal, row-major n x ldv) with the Krylov-Schur relation
+//     Op V[:, 0:nv] = V[:, 0:nv] T + V[:, nv:nv+bs] B E^T,
+// T (nv x nv, symmetric, its upper triangle kept on the device) and B = V[:, nv:nv+bs]^T Op V_last
+// (bs x bs; E^T selects the last block of columns).
+//   expand:  Yb = Op V_j (fused filter, bs columns); the first Gram-Schmidt pass h = V^T Yb is the
+//            new column block of T, W = Yb - V h, a second pass against V (DMMA), then
+//            V_{j+1} = CholQR2(W); a numerically rank-deficient W (shifted CholQR) is projected and
+//            factored once more;
+//   Ritz:    T = S Theta S^T (cuSOLVER); the residual of Ritz pair i is ||B s_i[nv-bs:nv]||, from
+//            bs x nv numbers on the host: no n-length work;
+//   restart: the `keep` largest Ritz pairs Y = V S[:, nv-keep:] become the new basis with
+//            T = diag(theta); the block V[:, nv:nv+bs] (orthogonal to all of V) continues the
+//            Krylov sequence, and its first expansion fills the coupling column block of T;
+//   stop:    every Ritz pair with theta >= theta_cut has residual <= tol_op max|theta|, at least one
+//            block of Ritz values lies below theta_cut, and the number of wanted pairs did not
+//            change since the previous restart.
+// theta_cut = sqrt(r) min(p(xi), p(eta)): below the filter's value at the interval edges and above
+// its value r min(p(xi), p(eta)) outside the margins (eq. (thresh)).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -39,15 +46,32 @@ pfe_status last_error(pfe_ctx *ctx, const char *what) {
   return PFE_OK;
 }
 
-// W (n x k, ld ldw) -= V (n x nv, ld ldv) (V^T W), twice (classical Gram-Schmidt with reorthogonalisation)
-pfe_status cgs2(pfe_ctx *ctx, const double *V, int64_t ldv, int32_t nv, double *W, int64_t ldw, int32_t k,
-                double *h, double *gw) {
-  if (nv <= 0 || k <= 0) return PFE_OK;
-  for (int pass = 0; pass < 2; ++pass) {
+// W (n x k, ld ldw) -= V (n x nv, ld ldv) (V^T W), `passes` times; h (col-major nv x k, ld nv)
+// receives the last V^T W
+void project(pfe_ctx *ctx, const double *V, int64_t ldv, int32_t nv, double *W, int64_t ldw, int32_t k, double *h,
+             double *gw, int passes) {
+  if (nv <= 0 || k <= 0) return;
+  for (int pass = 0; pass < passes; ++pass) {
     launch_gram(ctx->n, nv, k, V, ldv, W, ldw, 1.0, 0.0, h, nv, false, gw, ctx->stream);
     launch_update(ctx->n, k, nv, V, ldv, h, nv, -1.0, 1.0, W, ldw, ctx->stream);
   }
-  return last_error(ctx, "block reorthogonalisation");
+}
+
+// Orthonormalise W (n x bs, ld ldb) against V[:, 0:nv] and within itself: `first_passes` projection
+// passes and CholQR2, repeated with two passes when the block was numerically rank deficient (a
+// shifted factorisation).  The result is left in W.
+pfe_status orthonormalise_block(pfe_ctx *ctx, const double *V, int64_t ldv, int32_t nv, double *W, double *tmp,
+                                int64_t ldb, int32_t bs, double *h, double *gw, int first_passes) {
+  cudaStream_t s = ctx->stream;
+  for (int rep = 0; rep < 2; ++rep) {
+    project(ctx, V, ldv, nv, W, ldb, bs, h, gw, rep == 0 ? first_passes : 2);
+    double *res = nullptr;
+    bool shifted = false;
+    PFE_TRY(solver_cholqr2(ctx, W, tmp, bs, ldb, &res, &shifted));
+    if (res != W) launch_axpby<double>(ctx->n, bs, 1.0, res, ldb, 0.0, W, ldb, s);
+    if (!shifted) break;
+  }
+  return last_error(ctx, "block orthonormalisation");
 }
 
 }  // namespace
@@ -72,30 +96,34 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   maxbasis = (int32_t)std::min<int64_t>(maxbasis, (n - bs) / bs * bs);
   if (maxbasis < 3 * bs) return pfe_fail(ctx, PFE_E_ARG, "matrix too small for the block size");
   const int32_t keep_min = std::min(nev, maxbasis - 2 * bs);
-  const int64_t ldv = (maxbasis + bs + 3) / 4 * 4, ldb = (bs + 3) / 4 * 4;
+  const int64_t ldv = (maxbasis + bs + 3) / 4 * 4, ldb = (bs + 3) / 4 * 4, ldT = maxbasis;
   cudaStream_t s = ctx->stream;
-  // theta_cut from the filter's values at the interval edges
   const double pe = std::min(chebyshev_value(ctx->coef, ctx->m, ctx->xi), chebyshev_value(ctx->coef, ctx->m, ctx->eta));
   const double theta_cut = std::sqrt(ctx->p_rate) * pe;
-  // buffers: V, OV, Y, OY, Z (n x ldv); block buffers; small matrices
+  // n x ldv buffers: V (basis), Vn (next basis, or the wanted Ritz vectors), HW (products with H),
+  // Z = ctx->L (the returned eigenvectors)
   BKS_RESERVE(double, V, ctx->w_bks[0], (size_t)n * ldv);
-  BKS_RESERVE(double, OV, ctx->w_bks[1], (size_t)n * ldv);
-  BKS_RESERVE(double, Y, ctx->w_bks[2], (size_t)n * ldv);
-  BKS_RESERVE(double, OY, ctx->w_bks[3], (size_t)n * ldv);
-  BKS_RESERVE(double, Z, ctx->L, (size_t)n * ldv);  // final eigenvectors live in ctx->L
+  BKS_RESERVE(double, Vn, ctx->w_bks[1], (size_t)n * ldv);
+  BKS_RESERVE(double, HW, ctx->w_bks[2], (size_t)n * ldv);
+  BKS_RESERVE(double, Z, ctx->L, (size_t)n * ldv);
+  for (int i = 3; i < 5; ++i) dbuf_free(ctx->w_bks[i]);
   BKS_RESERVE(double, Xb, ctx->w_X, (size_t)n * ldb * 5);
   double *Yb = Xb + (size_t)n * ldb, *T0b = Yb + (size_t)n * ldb, *T1b = T0b + (size_t)n * ldb,
          *Wb = T1b + (size_t)n * ldb;
-  BKS_RESERVE(double, T, ctx->w_rr, (size_t)maxbasis * maxbasis + 3 * (size_t)maxbasis + 8);
-  // evals: Ritz values; dres: the kept Ritz values (residual input); rout: residual norms squared
-  double *evals = T + (size_t)maxbasis * maxbasis, *dres = evals + maxbasis, *rout = dres + maxbasis;
-  BKS_RESERVE(double, h, ctx->w_small2, (size_t)(maxbasis + bs) * std::max(bs, 1) + 8);
+  // small: Tm (maxbasis x maxbasis col-major: the upper triangle of T), A (Ritz vectors S, ld nv),
+  // evals, fin_lam / fin_r2 (the final step's eigenvalues and squared residuals), Bm (bs x bs)
+  const size_t mb = (size_t)maxbasis;
+  BKS_RESERVE(double, Tm, ctx->w_rr, 2 * mb * mb + 3 * mb + (size_t)bs * bs + 8);
+  double *A = Tm + mb * mb, *evals = A + mb * mb, *fin_lam = evals + mb, *fin_r2 = fin_lam + mb, *Bm = fin_r2 + mb;
+  BKS_RESERVE(double, h, ctx->w_small2, (mb + bs) * (size_t)std::max(bs, 1) + 8);
   BKS_RESERVE(double, gw, ctx->w_gram,
-              std::max(gram_work(n, maxbasis + bs, bs, false), gram_work(n, maxbasis, maxbasis, false)));
+              std::max({gram_work(n, maxbasis + bs, bs, false), gram_work(n, maxbasis, maxbasis, false),
+                        gram_work(n, bs, bs, true)}));  // CholQR2 reuses this buffer: it must not grow
   BKS_RESERVE(double, red, ctx->w_red, colreduce_work(n, maxbasis) + 8);
   BKS_RESERVE(int, info, ctx->w_info, 4);
-  for (double *p : {V, OV, Y, OY, Z}) launch_zero<double>(p, n * ldv, s);
+  launch_zero<double>(V, n * ldv, s);
   launch_zero<double>(Xb, n * ldb * 5, s);
+  launch_zero<double>(Tm, (int64_t)(mb * mb), s);
   const double tol = ctx->p_tol;
   const int max_restarts = std::max(ctx->p_max_iters, 1);
   double tol_op = 1e-10, t_filter = 0.0, t_orth = 0.0, t_rr = 0.0;
@@ -111,17 +139,15 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
     acc += ms * 1e-3;
     cudaEventRecord(e0, s);
   };
+  const Bsr<double> Hb{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>()};
   cudaEventRecord(e0, s);
   // start block: Philox normals of stream 0, orthonormalised
   launch_fill_normal<double>(ctx->p_seed, 0u, n, bs, 0, Wb, ldb, s);
-  {
-    double *res = nullptr;
-    PFE_TRY(solver_cholqr2(ctx, Wb, T0b, bs, ldb, &res));
-    launch_axpby<double>(n, bs, 1.0, res, ldb, 0.0, V, ldv, s);
-  }
+  PFE_TRY(orthonormalise_block(ctx, V, ldv, 0, Wb, T0b, ldb, bs, h, gw, 2));
+  launch_axpby<double>(n, bs, 1.0, Wb, ldb, 0.0, V, ldv, s);
   int32_t nv = 0, restarts = 0, prev_nwant = -1, nf = 0;
   pfe_status result = PFE_E_NOCONV;
-  std::vector<double> hev, hres;
+  std::vector<double> hev, hS, hB, hres, hkeep;
   std::vector<int32_t> sel_cols;
   std::vector<double> sel_lam, sel_res;
   for (;;) {
@@ -134,55 +160,65 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
       matvecs += (int64_t)bs * ctx->m;
       f_launch += std::max(ctx->m, 1);
       f_cols += (int64_t)bs * std::max(ctx->m, 1);
-      launch_axpby<double>(n, bs, 1.0, Yb, ldb, 0.0, OV + nv, ldv, s);
       launch_axpby<double>(n, bs, 1.0, Yb, ldb, 0.0, Wb, ldb, s);
-      double *res = nullptr;
-      for (int rep = 0; rep < 2; ++rep) {
-        PFE_TRY(cgs2(ctx, V, ldv, nv + bs, Wb, ldb, bs, h, gw));
-        PFE_TRY(solver_cholqr2(ctx, Wb, T0b, bs, ldb, &res));
-        if (res != Wb) launch_axpby<double>(n, bs, 1.0, res, ldb, 0.0, Wb, ldb, s);
-      }
+      // first pass: T[0:nv+bs, nv:nv+bs] = V^T Op V_j, then W -= V T[0:nv+bs, nv:nv+bs]
+      double *Tcol = Tm + (size_t)nv * ldT;
+      launch_gram(n, nv + bs, bs, V, ldv, Wb, ldb, 1.0, 0.0, Tcol, ldT, false, gw, s);
+      launch_update(n, bs, nv + bs, V, ldv, Tcol, ldT, -1.0, 1.0, Wb, ldb, s);
+      PFE_TRY(orthonormalise_block(ctx, V, ldv, nv + bs, Wb, T0b, ldb, bs, h, gw, 1));
       launch_axpby<double>(n, bs, 1.0, Wb, ldb, 0.0, V + nv + bs, ldv, s);
-      PFE_TRY(last_error(ctx, "expansion"));
       nv += bs;
       timed(t_orth);
     }
-    // ---- Rayleigh-Ritz of Op on span(V): T = V^T OV, eigen-decomposition
-    launch_gram(n, nv, nv, V, ldv, OV, ldv, 1.0, 0.0, T, nv, false, gw, s);
+    // ---- Ritz pairs of T; B = V_new^T Op V_last (Yb holds Op V_last)
+    launch_gram(n, bs, bs, V + nv, ldv, Yb, ldb, 1.0, 0.0, Bm, bs, false, gw, s);
+    PFE_CUDA_TRY(ctx, cudaMemcpy2DAsync(A, sizeof(double) * nv, Tm, sizeof(double) * ldT, sizeof(double) * nv, nv,
+                                        cudaMemcpyDeviceToDevice, s));
     int lw = 0;
     PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, nv,
-                                                    T, nv, evals, &lw));
+                                                    A, nv, evals, &lw));
     BKS_RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
-    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, nv, T, nv,
+    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, nv, A, nv,
                                          evals, work, lw, info));
     hev.resize(nv);
+    hS.resize((size_t)bs * nv);
+    hB.resize((size_t)bs * bs);
     int hinfo = 0;
     PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hev.data(), evals, sizeof(double) * nv, cudaMemcpyDeviceToHost, s));
+    // the last bs rows of every Ritz vector s_i (column i of A, ld nv)
+    PFE_CUDA_TRY(ctx, cudaMemcpy2DAsync(hS.data(), sizeof(double) * bs, A + (nv - bs), sizeof(double) * nv,
+                                        sizeof(double) * bs, nv, cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hB.data(), Bm, sizeof(double) * bs * bs, cudaMemcpyDeviceToHost, s));
     PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
     PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    PFE_TRY(last_error(ctx, "Ritz pairs"));
     if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge");
-    // wanted: Ritz values >= theta_cut (they are the last ones: ascending order)
+    timed(t_rr);
+    // residuals ||B s_i,last|| (B col-major bs x bs)
+    hres.assign(nv, 0.0);
+    for (int32_t i = 0; i < nv; ++i) {
+      const double *sl = hS.data() + (size_t)i * bs;
+      double acc = 0.0;
+      for (int32_t r = 0; r < bs; ++r) {
+        double v = 0.0;
+        for (int32_t c = 0; c < bs; ++c) v += hB[(size_t)c * bs + r] * sl[c];
+        acc += v * v;
+      }
+      hres[i] = std::sqrt(acc);
+    }
+    // wanted: Ritz values >= theta_cut (the last ones: ascending order)
     int32_t nwant = 0;
-    for (int32_t i = 0; i < nv; ++i)
+    double thmax = 0.0;
+    for (int32_t i = 0; i < nv; ++i) {
       if (hev[i] >= theta_cut) ++nwant;
+      thmax = std::max(thmax, std::fabs(hev[i]));
+    }
     int32_t keep = std::max(nwant + bs, keep_min);
     keep = std::min(keep, nv - bs);
     keep = std::max(keep, nwant);
-    // the kept Ritz pairs: Y = V S[:, nv-keep:], OY = OV S[:, nv-keep:]
-    launch_update(n, keep, nv, V, ldv, T + (size_t)(nv - keep) * nv, nv, 1.0, 0.0, Y, ldv, s);
-    launch_update(n, keep, nv, OV, ldv, T + (size_t)(nv - keep) * nv, nv, 1.0, 0.0, OY, ldv, s);
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(dres, evals + (nv - keep), sizeof(double) * keep, cudaMemcpyDeviceToDevice, s));
-    launch_col_resid2(n, keep, OY, Y, ldv, dres, rout, red, s);
-    hres.resize(keep);
-    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(hres.data(), rout, sizeof(double) * keep, cudaMemcpyDeviceToHost, s));
-    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    PFE_TRY(last_error(ctx, "Ritz pairs"));
-    timed(t_rr);
-    double thmax = 0.0;
-    for (int32_t i = 0; i < nv; ++i) thmax = std::max(thmax, std::fabs(hev[i]));
     int32_t nconv = 0;
-    for (int32_t i = keep - nwant; i < keep; ++i)
-      if (std::sqrt(std::max(hres[i], 0.0)) <= tol_op * thmax) ++nconv;
+    for (int32_t i = nv - nwant; i < nv; ++i)
+      if (hres[i] <= tol_op * thmax) ++nconv;
     if (nwant > nv - bs) {  // the wanted Ritz values fill the basis: completeness cannot be shown
       result = PFE_E_CAPACITY;
       break;
@@ -190,31 +226,34 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
     const bool done = nwant == nconv && nwant == prev_nwant;
     prev_nwant = nwant;
     if (done) {
-      // ---- Rayleigh-Ritz with H on the wanted Op-eigenvectors Yw = Y[:, keep - nwant : keep]
-      const double *Yw = Y + (keep - nwant);
+      // ---- Rayleigh-Ritz with H on the wanted Op-eigenvectors Yw = V S[:, nv - nwant : nv] (in Vn)
       const int32_t k = nwant;
       sel_cols.clear();
       sel_lam.clear();
       sel_res.clear();
       bool bad = false;
       if (k > 0) {
-        launch_bsr_step<double>(Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>()},
-                                MODE_SPMM, k, ldv, Yw, nullptr, OV, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+        launch_update(n, k, nv, V, ldv, A + (size_t)(nv - k) * nv, nv, 1.0, 0.0, Vn, ldv, s);
+        launch_bsr_step<double>(Hb, MODE_SPMM, k, ldv, Vn, nullptr, HW, nullptr, 1.0, 0.0, 0.0, 0.0, s);
         matvecs += k;
-        launch_gram(n, k, k, Yw, ldv, OV, ldv, 1.0, 0.0, T, k, false, gw, s);
+        {
+          BKS_RESERVE(double, gw2, ctx->w_gram, gram_work(n, k, k, false));
+          gw = gw2;  // the buffer may have grown
+        }
+        double *G = Tm;  // T is rebuilt by the restart below if the iteration has to continue
+        launch_gram(n, k, k, Vn, ldv, HW, ldv, 1.0, 0.0, G, k, false, gw, s);
         PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k,
-                                                        T, k, evals, &lw));
+                                                        G, k, fin_lam, &lw));
         BKS_RESERVE(double, work2, ctx->w_cs_work, (size_t)std::max(lw, 1));
-        PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, T, k,
-                                             evals, work2, lw, info));
-        launch_update(n, k, k, Yw, ldv, T, k, 1.0, 0.0, Z, ldv, s);  // U = Yw Q
-        launch_bsr_step<double>(Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>()},
-                                MODE_SPMM, k, ldv, Z, nullptr, OV, nullptr, 1.0, 0.0, 0.0, 0.0, s);
+        PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, G, k,
+                                             fin_lam, work2, lw, info));
+        launch_update(n, k, k, Vn, ldv, G, k, 1.0, 0.0, Z, ldv, s);  // U = Yw Q
+        launch_bsr_step<double>(Hb, MODE_SPMM, k, ldv, Z, nullptr, HW, nullptr, 1.0, 0.0, 0.0, 0.0, s);
         matvecs += k;
-        launch_col_resid2(n, k, OV, Z, ldv, evals, rout, red, s);
+        launch_col_resid2(n, k, HW, Z, ldv, fin_lam, fin_r2, red, s);
         std::vector<double> lam(k), r2(k);
-        PFE_CUDA_TRY(ctx, cudaMemcpyAsync(lam.data(), evals, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-        PFE_CUDA_TRY(ctx, cudaMemcpyAsync(r2.data(), rout, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        PFE_CUDA_TRY(ctx, cudaMemcpyAsync(lam.data(), fin_lam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        PFE_CUDA_TRY(ctx, cudaMemcpyAsync(r2.data(), fin_r2, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
         PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
         PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge");
@@ -227,8 +266,8 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
           sel_lam.push_back(lam[j]);
           sel_res.push_back(rel * ctx->lmax);
         }
+        timed(t_rr);
       }
-      timed(t_rr);
       if (!bad) {
         result = (nwant >= maxbasis - bs) ? PFE_E_CAPACITY : PFE_OK;
         nf = (int32_t)sel_cols.size();
@@ -240,22 +279,22 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
         break;
       }
       tol_op *= 1e-2;  // the Op-residuals were not yet small enough for the H-residuals
-      // OV was overwritten by the final Rayleigh-Ritz: OY still holds Op Y for the restart below
     }
     if (++restarts > max_restarts) {
       result = PFE_E_NOCONV;
       break;
     }
-    // ---- thick restart: the kept Ritz pairs, then the continuation block V[:, nv : nv + bs]
+    // ---- thick restart: [V S[:, nv-keep:nv] | V[:, nv:nv+bs]] becomes the basis, T = diag(theta_kept)
+    launch_update(n, keep, nv, V, ldv, A + (size_t)(nv - keep) * nv, nv, 1.0, 0.0, Vn, ldv, s);
     launch_axpby<double>(n, bs, 1.0, V + nv, ldv, 0.0, Wb, ldb, s);
-    launch_axpby<double>(n, keep, 1.0, Y, ldv, 0.0, V, ldv, s);
-    launch_axpby<double>(n, keep, 1.0, OY, ldv, 0.0, OV, ldv, s);
-    {
-      double *res = nullptr;
-      PFE_TRY(cgs2(ctx, V, ldv, keep, Wb, ldb, bs, h, gw));
-      PFE_TRY(solver_cholqr2(ctx, Wb, T0b, bs, ldb, &res));
-      launch_axpby<double>(n, bs, 1.0, res, ldb, 0.0, V + keep, ldv, s);
-    }
+    std::swap(V, Vn);
+    PFE_TRY(orthonormalise_block(ctx, V, ldv, keep, Wb, T0b, ldb, bs, h, gw, 2));
+    launch_axpby<double>(n, bs, 1.0, Wb, ldb, 0.0, V + keep, ldv, s);
+    launch_zero<double>(Tm, (int64_t)(mb * mb), s);
+    hkeep.assign(hev.end() - keep, hev.end());
+    PFE_CUDA_TRY(ctx, cudaMemcpy2DAsync(Tm, sizeof(double) * (ldT + 1), hkeep.data(), sizeof(double), sizeof(double),
+                                        keep, cudaMemcpyHostToDevice, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // hkeep must outlive its copy
     PFE_TRY(last_error(ctx, "restart"));
     nv = keep;
     timed(t_orth);

@@ -13,60 +13,10 @@
 #include <tuple>
 
 #include "pfe_internal.h"
+#include "vec_io.cuh"
 
 namespace pfe {
 namespace {
-
-// ---- vector loads/stores of CPL adjacent elements ------------------------------------
-__device__ __forceinline__ void ldg_n(const double *p, double (&v)[1]) { v[0] = __ldg(p); }
-__device__ __forceinline__ void ldg_n(const double *p, double (&v)[2]) {
-  double2 t = __ldg(reinterpret_cast<const double2 *>(p));
-  v[0] = t.x;
-  v[1] = t.y;
-}
-__device__ __forceinline__ void ldg_n(const float *p, float (&v)[1]) { v[0] = __ldg(p); }
-__device__ __forceinline__ void ldg_n(const float *p, float (&v)[2]) {
-  float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-  v[0] = t.x;
-  v[1] = t.y;
-}
-__device__ __forceinline__ void ldg_n(const float *p, float (&v)[4]) {
-  float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-  v[0] = t.x;
-  v[1] = t.y;
-  v[2] = t.z;
-  v[3] = t.w;
-}
-__device__ __forceinline__ void ld_n(const double *p, double (&v)[1]) { v[0] = *p; }
-__device__ __forceinline__ void ld_n(const double *p, double (&v)[2]) {
-  double2 t = *reinterpret_cast<const double2 *>(p);
-  v[0] = t.x;
-  v[1] = t.y;
-}
-__device__ __forceinline__ void ld_n(const float *p, float (&v)[1]) { v[0] = *p; }
-__device__ __forceinline__ void ld_n(const float *p, float (&v)[2]) {
-  float2 t = *reinterpret_cast<const float2 *>(p);
-  v[0] = t.x;
-  v[1] = t.y;
-}
-__device__ __forceinline__ void ld_n(const float *p, float (&v)[4]) {
-  float4 t = *reinterpret_cast<const float4 *>(p);
-  v[0] = t.x;
-  v[1] = t.y;
-  v[2] = t.z;
-  v[3] = t.w;
-}
-__device__ __forceinline__ void st_n(double *p, const double (&v)[1]) { *p = v[0]; }
-__device__ __forceinline__ void st_n(double *p, const double (&v)[2]) {
-  *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
-}
-__device__ __forceinline__ void st_n(float *p, const float (&v)[1]) { *p = v[0]; }
-__device__ __forceinline__ void st_n(float *p, const float (&v)[2]) {
-  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-}
-__device__ __forceinline__ void st_n(float *p, const float (&v)[4]) {
-  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
 
 // ---- the fused step -------------------------------------------------------------------
 // SPMM : Z = alpha A X
@@ -337,19 +287,22 @@ bool aligned(const void *p, size_t a) { return p == nullptr || (reinterpret_cast
 // Kernel shape of the fused step: 0 = warp per (atom, chunk), 1 = CTA per 8 atoms x chunk,
 // 2 = as 0 with two blocks in flight, 3 = as 1 with two blocks in flight, 4 = rows staged in
 // shared memory by cp.async, four blocks ahead (16-byte lanes only; else shape 0), 5 and 6 = as
-// 0 and 1 compiled for five resident CTAs per SM (at most 51 registers a thread).
+// 0 and 1 compiled for five resident CTAs per SM (at most 51 registers a thread).  Shapes 7, 8, 9
+// run on the rank-1 form of the operator when it has one (r1_kernels.cu: warp per (atom, chunk);
+// five resident CTAs; two blocks in flight); without it they fall back to shape 0.
 // A forced shape (set_step_variant) wins; otherwise the autotuner's choice for (type, columns per
-// lane, column chunks) is used, and the default 0 before any tuning.
+// lane, column chunks, rank-1 form present) is used, and the default 0 before any tuning.
 namespace {
-constexpr int kVariants = 7;
+constexpr int kVariants = 7, kR1Variants = 3;
 int g_forced[2] = {-1, -1};  // [double, float]
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tuned;  // (is_float, CPL, min(nchunk, 16)) -> shape
+std::mutex g_tune_run_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;  // (is_float, CPL, min(nchunk, 16), rank-1) -> shape
 
-int pick_variant(int is_float, int cpl, int32_t nchunk) {
+int pick_variant(int is_float, int cpl, int32_t nchunk, bool r1) {
   if (g_forced[is_float] >= 0) return g_forced[is_float];
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned.find(std::make_tuple(is_float, cpl, std::min(nchunk, 16)));
+  auto it = g_tuned.find(std::make_tuple(is_float, cpl, std::min(nchunk, 16), r1 ? 1 : 0));
   return it == g_tuned.end() ? 0 : it->second;
 }
 }  // namespace
@@ -370,6 +323,13 @@ int cpl_for<float>(int32_t k, int64_t ld, bool al16, bool al8) {
 template <typename T>
 void dispatch_cpl(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
                   T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s) {
+  if (variant >= kVariants) {
+    if (A.u && A.dg && A.rp1 && A.ci1) {
+      dispatch_r1<T>(cpl, variant - kVariants, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
+      return;
+    }
+    variant = 0;
+  }
   if (cpl == 4)
     dispatch_variant<T, (sizeof(T) == 4 ? 4 : 2)>(variant, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
   else if (cpl == 2)
@@ -388,7 +348,14 @@ void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, c
   if (g_forced[is_float] >= 0) return;
   const int cpl = cpl_for<T>(k, ld, aligned(X, 16) && aligned(scratch, 16), aligned(X, 8) && aligned(scratch, 8));
   const int32_t nchunk = (k + 32 * cpl - 1) / (32 * cpl);
-  const auto key = std::make_tuple(is_float, cpl, std::min(nchunk, 16));
+  const bool r1 = A.u != nullptr;
+  const auto key = std::make_tuple(is_float, cpl, std::min(nchunk, 16), r1 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tuned.count(key)) return;
+  }
+  // one tuning run at a time (host threads of a batched solve would otherwise time each other)
+  std::lock_guard<std::mutex> run_lock(g_tune_run_mu);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_tuned.count(key)) return;
@@ -401,7 +368,7 @@ void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, c
   }
   float best = 1e30f;
   int best_v = 0;
-  for (int v = 0; v < kVariants; ++v) {
+  for (int v = 0; v < kVariants + (r1 ? kR1Variants : 0); ++v) {
     float t = 1e30f;
     for (int trial = 0; trial < 2; ++trial) {
       cudaEventRecord(e0, s);
@@ -431,7 +398,7 @@ void launch_bsr_step<double>(const Bsr<double> &A, int mode, int32_t k, int64_t 
   if (k <= 0 || A.n_atoms <= 0) return;
   const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
   const int cpl = cpl_for<double>(k, ld, al16, false);
-  const int v = pick_variant(0, cpl, (k + 32 * cpl - 1) / (32 * cpl));
+  const int v = pick_variant(0, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
   dispatch_cpl<double>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
@@ -442,7 +409,7 @@ void launch_bsr_step<float>(const Bsr<float> &A, int mode, int32_t k, int64_t ld
   const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
   const bool al8 = aligned(X, 8) && aligned(W, 8) && aligned(Z, 8) && aligned(Y, 8);
   const int cpl = cpl_for<float>(k, ld, al16, al8);
-  const int v = pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl));
+  const int v = pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
   dispatch_cpl<float>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
@@ -537,31 +504,74 @@ __global__ void k_chain_m(int32_t n_atoms, const int32_t *__restrict__ rp, const
   mbar[i] = -off / (2.0 * mass[i]) - dia / mass[i];
 }
 
-// hbar[9p + 3r + s] += alpha * sum_c A[3i + r, c] * Tm[3j + s, c]; one warp per atom row i
-template <typename T>
-__global__ void k_outer_accum(int32_t n_atoms, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                              int32_t k, int64_t ld, const T *__restrict__ A, const T *__restrict__ Tm, double alpha,
-                              double *hbar) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n_atoms) return;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    const int64_t j = ci[p];
-    double s[9];
+// Segment form of the adjoint's pattern-restricted outer products:
+//   hbar[9p + 3r + s] += sum_q alpha_q sum_c A_q[3i + r, c] * T_q[3j + s, c],   block p = (i, j),
+// with A_q = A0 + q * stride, T_q = T0 + q * stride (q = 0 .. nq - 1), alpha_q = alpha except
+// alpha_0 = alpha0.  One group of four lanes per stored block; the lanes split the contraction over
+// (q, column pairs) and meet in two shuffle steps.  The row i of block p comes from a binary search
+// of row_ptr.  ld is even and A0, T0 and stride keep every row start 16-byte aligned.
+__global__ void __launch_bounds__(256) k_outer_accum_seg(int32_t n_atoms, int64_t nnzb, const int32_t *__restrict__ rp,
+                                                         const int32_t *__restrict__ ci, int32_t k, int64_t ld,
+                                                         int32_t nq, int64_t stride, const double *__restrict__ A0,
+                                                         const double *__restrict__ T0, double alpha0, double alpha,
+                                                         double *__restrict__ hbar) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const int l4 = threadIdx.x & 3;
+  const bool live = g < nnzb;
+  const int64_t p = live ? g : nnzb - 1;
+  int32_t lo = 0, hi = n_atoms;  // largest i with rp[i] <= p
+  while (hi - lo > 1) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (rp[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  const int64_t i = lo, j = ci[p];
+  double s[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) s[t] = 0.0;
-    for (int c = lane; c < k; c += 32) {
-      const double a0 = A[(3 * i) * ld + c], a1 = A[(3 * i + 1) * ld + c], a2 = A[(3 * i + 2) * ld + c];
-      const double t0 = Tm[(3 * j) * ld + c], t1 = Tm[(3 * j + 1) * ld + c], t2 = Tm[(3 * j + 2) * ld + c];
-      s[0] += a0 * t0; s[1] += a0 * t1; s[2] += a0 * t2;
-      s[3] += a1 * t0; s[4] += a1 * t1; s[5] += a1 * t2;
-      s[6] += a2 * t0; s[7] += a2 * t1; s[8] += a2 * t2;
+  for (int t = 0; t < 9; ++t) s[t] = 0.0;
+  for (int32_t q = 0; q < nq; ++q) {
+    const double *a = A0 + q * stride + 3 * i * ld, *t = T0 + q * stride + 3 * j * ld;
+    double u[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = 0.0;
+    for (int32_t c = 2 * l4; c < k; c += 8) {
+      if (c + 1 < k) {
+        const double2 a0 = __ldg(reinterpret_cast<const double2 *>(a + c));
+        const double2 a1 = __ldg(reinterpret_cast<const double2 *>(a + ld + c));
+        const double2 a2 = __ldg(reinterpret_cast<const double2 *>(a + 2 * ld + c));
+        const double2 t0 = __ldg(reinterpret_cast<const double2 *>(t + c));
+        const double2 t1 = __ldg(reinterpret_cast<const double2 *>(t + ld + c));
+        const double2 t2 = __ldg(reinterpret_cast<const double2 *>(t + 2 * ld + c));
+        u[0] = fma(a0.x, t0.x, fma(a0.y, t0.y, u[0]));
+        u[1] = fma(a0.x, t1.x, fma(a0.y, t1.y, u[1]));
+        u[2] = fma(a0.x, t2.x, fma(a0.y, t2.y, u[2]));
+        u[3] = fma(a1.x, t0.x, fma(a1.y, t0.y, u[3]));
+        u[4] = fma(a1.x, t1.x, fma(a1.y, t1.y, u[4]));
+        u[5] = fma(a1.x, t2.x, fma(a1.y, t2.y, u[5]));
+        u[6] = fma(a2.x, t0.x, fma(a2.y, t0.y, u[6]));
+        u[7] = fma(a2.x, t1.x, fma(a2.y, t1.y, u[7]));
+        u[8] = fma(a2.x, t2.x, fma(a2.y, t2.y, u[8]));
+      } else {
+        const double a0 = a[c], a1 = a[ld + c], a2 = a[2 * ld + c];
+        const double t0 = t[c], t1 = t[ld + c], t2 = t[2 * ld + c];
+        u[0] = fma(a0, t0, u[0]); u[1] = fma(a0, t1, u[1]); u[2] = fma(a0, t2, u[2]);
+        u[3] = fma(a1, t0, u[3]); u[4] = fma(a1, t1, u[4]); u[5] = fma(a1, t2, u[5]);
+        u[6] = fma(a2, t0, u[6]); u[7] = fma(a2, t1, u[7]); u[8] = fma(a2, t2, u[8]);
+      }
     }
+    const double w = q == 0 ? alpha0 : alpha;
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
-      for (int o = 16; o > 0; o >>= 1) s[t] += __shfl_xor_sync(0xffffffffu, s[t], o);
-    if (lane == 0)
-      for (int t = 0; t < 9; ++t) hbar[9 * (int64_t)p + t] += alpha * s[t];
+    for (int e = 0; e < 9; ++e) s[e] = fma(w, u[e], s[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    s[e] += __shfl_xor_sync(0xffffffffu, s[e], 1);
+    s[e] += __shfl_xor_sync(0xffffffffu, s[e], 2);
+  }
+  if (live) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+      if ((e & 3) == l4) hbar[9 * p + e] += s[e];
   }
 }
 }  // namespace
@@ -585,13 +595,12 @@ void launch_chain_springs(int32_t n_atoms, const int32_t *rp, const int32_t *ci,
   if (n_atoms > 0) PFE_LAUNCH k_chain_m<<<(unsigned)((n_atoms + 255) / 256), 256, 0, s>>>(n_atoms, rp, ci, H, mass, hbar, mbar);
 }
 
-template <typename T>
-void launch_outer_accum(const Bsr<T> &pattern, int32_t k, int64_t ld, const T *A, const T *Tm, double alpha,
-                        double *hbar, cudaStream_t s) {
-  const int64_t blocks = ((int64_t)pattern.n_atoms * 32 + 255) / 256;
-  PFE_LAUNCH k_outer_accum<T><<<(unsigned)blocks, 256, 0, s>>>(pattern.n_atoms, pattern.rp, pattern.ci, k, ld, A, Tm, alpha, hbar);
+void launch_outer_accum_seg(const Bsr<double> &pattern, int64_t nnzb, int32_t k, int64_t ld, int32_t nq, int64_t stride,
+                            const double *A0, const double *T0, double alpha0, double alpha, double *hbar, cudaStream_t s) {
+  if (nq <= 0 || nnzb <= 0 || k <= 0) return;
+  const int64_t blocks = (4 * nnzb + 255) / 256;
+  PFE_LAUNCH k_outer_accum_seg<<<(unsigned)blocks, 256, 0, s>>>(pattern.n_atoms, nnzb, pattern.rp, pattern.ci, k, ld, nq,
+                                                                 stride, A0, T0, alpha0, alpha, hbar);
 }
-template void launch_outer_accum<double>(const Bsr<double> &, int32_t, int64_t, const double *, const double *, double,
-                                         double *, cudaStream_t);
 
 }  // namespace pfe

@@ -44,6 +44,14 @@ struct Bsr {
   const int32_t *rp = nullptr;
   const int32_t *ci = nullptr;
   const T *vals = nullptr;
+  // Optional rank-1 form of the same operator (central-force networks): every off-diagonal block
+  // is -u u^T.  rp1/ci1: the pattern without the diagonal blocks; u: 3 values per off-diagonal
+  // block; dg: the symmetric diagonal block of each atom as (xx, xy, xz, yy, yz, zz).  Null when
+  // the matrix does not have that form.
+  const int32_t *rp1 = nullptr;
+  const int32_t *ci1 = nullptr;
+  const T *u = nullptr;
+  const T *dg = nullptr;
 };
 
 // Step modes of the fused BSR kernel (row-major n x k multivectors with row stride ld):
@@ -62,6 +70,14 @@ void set_step_variant(int is_float, int variant);
 int step_variant(int is_float);
 template <typename T>
 void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, cudaStream_t s);
+// the step on the rank-1 form (A.u, A.dg; shapes 0..2 of r1_kernels.cu)
+template <typename T>
+void dispatch_r1(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
+                 T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s);
+// rank-1 form of alpha (H - shift I); *bad (device) is set to 1 if an off-diagonal block is not -u u^T
+void launch_build_r1(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha, double shift,
+                     int32_t *rp1, int32_t *ci1, double *u64, double *dg64, float *u32, float *dg32, int32_t *bad,
+                     cudaStream_t s);
 
 // a0: H = Delta / sqrt(m_i m_j) per block; also the row index of each block
 void launch_mass_weight(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *delta, const double *mass,
@@ -73,10 +89,11 @@ void launch_filter_matrix(int32_t n_atoms, const int32_t *rp, const int32_t *ci,
 void launch_chain_springs(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, const double *mass,
                           int64_t nbonds, const int32_t *bi, const int32_t *bj, const double *rhat, const double *hbar,
                           double *kbar, double *mbar, cudaStream_t s);
-// Adjoint outer-product accumulation: hbar[p] += alpha * sum_c A[i, c] T[j, c] over block p = (i, j)
-template <typename T>
-void launch_outer_accum(const Bsr<T> &pattern, int32_t k, int64_t ld, const T *A, const T *Tm, double alpha,
-                        double *hbar, cudaStream_t s);
+// Adjoint outer products over one checkpoint segment:
+// hbar[9p + 3r + s] += sum_q alpha_q sum_c A_q[3i + r, c] T_q[3j + s, c] over every stored block p = (i, j),
+// A_q = A0 + q stride, T_q = T0 + q stride, alpha_0 = alpha0, alpha_q = alpha (q >= 1); ld even
+void launch_outer_accum_seg(const Bsr<double> &pattern, int64_t nnzb, int32_t k, int64_t ld, int32_t nq, int64_t stride,
+                            const double *A0, const double *T0, double alpha0, double alpha, double *hbar, cudaStream_t s);
 
 // --------------------------------------------------------------------------------------
 // Dense helpers (row-major n x k blocks with row stride ld unless stated)
@@ -195,6 +212,11 @@ struct pfe_ctx {
   pfe::DBuf rp, ci, H, mass, Hs64, Hs32;
   double hs_c = 0, hs_d = 0;  // transform the filter matrices were built for
   bool hs_valid = false, hs32_valid = false;
+  // rank-1 form of the filter operator (central-force networks; see r1_kernels.cu):
+  // r1_state -1 = not checked, 0 = H has no such form, 1 = built (r1_32: the FP32 copy too)
+  pfe::DBuf r1_rp, r1_ci, r1_u64, r1_dg64, r1_u32, r1_dg32, r1_flag;
+  int r1_state = -1;
+  bool r1_32 = false;
 
   // parameters
   int32_t p_degree = 0;
@@ -215,6 +237,8 @@ struct pfe_ctx {
   int p_method = 0;
   int32_t p_block = 64;
   double p_basis_factor = 3.0;
+  int32_t p_batch_threads = 0;
+  int p_rank1 = 1;
 
   // state
   bool has_interval = false;
@@ -254,7 +278,9 @@ pfe_status solver_ensure_filter(pfe_ctx *ctx);
 pfe_status solver_ensure_hs(pfe_ctx *ctx, bool need32);
 pfe_status solver_count(pfe_ctx *ctx);
 pfe_status solver_window(pfe_ctx *ctx, double *out);
-pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result);
+// *shifted (optional): a factorisation broke down and was shifted (the block was numerically rank deficient)
+pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result,
+                          bool *shifted = nullptr);
 pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1);
 double solver_now();
 }  // namespace pfe

@@ -7,10 +7,12 @@
 //          W = H X ; Rayleigh-Ritz ; residuals ; lock } .
 // The only device-to-host traffic per iteration is the q Ritz values and residual norms.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "pfe_internal.h"
 
@@ -50,8 +52,27 @@ T *reserve(pfe_ctx *ctx, DBuf &b, size_t count, pfe_status *st) {
   }
 
 Bsr<double> bsr_H(const pfe_ctx *ctx) { return Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>()}; }
-Bsr<double> bsr_Hs64(const pfe_ctx *ctx) { return Bsr<double>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs64.as<double>()}; }
-Bsr<float> bsr_Hs32(const pfe_ctx *ctx) { return Bsr<float>{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs32.as<float>()}; }
+// the filter operator A = (2/d)(H - cI); with its rank-1 form when that was built and is enabled
+Bsr<double> bsr_Hs64(const pfe_ctx *ctx) {
+  Bsr<double> A{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs64.as<double>()};
+  if (ctx->p_rank1 && ctx->r1_state == 1) {
+    A.rp1 = ctx->r1_rp.as<int32_t>();
+    A.ci1 = ctx->r1_ci.as<int32_t>();
+    A.u = ctx->r1_u64.as<double>();
+    A.dg = ctx->r1_dg64.as<double>();
+  }
+  return A;
+}
+Bsr<float> bsr_Hs32(const pfe_ctx *ctx) {
+  Bsr<float> A{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs32.as<float>()};
+  if (ctx->p_rank1 && ctx->r1_state == 1 && ctx->r1_32) {
+    A.rp1 = ctx->r1_rp.as<int32_t>();
+    A.ci1 = ctx->r1_ci.as<int32_t>();
+    A.u = ctx->r1_u32.as<float>();
+    A.dg = ctx->r1_dg32.as<float>();
+  }
+  return A;
+}
 
 pfe_status check_launch(pfe_ctx *ctx, const char *what) {
   cudaError_t e = cudaGetLastError();
@@ -180,6 +201,35 @@ pfe_status ensure_hs(pfe_ctx *ctx, bool need32) {
   launch_filter_matrix(ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>(), 2.0 / ctx->td, ctx->tc,
                        h64, h32, ctx->stream);
   PFE_TRY(check_launch(ctx, "filter matrix"));
+  if (ctx->p_rank1 && ctx->r1_state != 0 && ctx->nnzb > ctx->N) {
+    const int64_t noff = ctx->nnzb - ctx->N;
+    RESERVE(int32_t, rp1, ctx->r1_rp, (size_t)ctx->N + 1);
+    RESERVE(int32_t, ci1, ctx->r1_ci, (size_t)noff);
+    RESERVE(double, u64, ctx->r1_u64, 3 * (size_t)noff);
+    RESERVE(double, dg64, ctx->r1_dg64, 6 * (size_t)ctx->N);
+    float *u32 = nullptr, *dg32 = nullptr;
+    const bool with32 = need32 || (same && ctx->hs32_valid);  // the FP32 operator in use after this call
+    if (with32) {
+      RESERVE(float, pu, ctx->r1_u32, 3 * (size_t)noff);
+      RESERVE(float, pd, ctx->r1_dg32, 6 * (size_t)ctx->N);
+      u32 = pu;
+      dg32 = pd;
+    }
+    RESERVE(int32_t, flag, ctx->r1_flag, 1);
+    PFE_CUDA_TRY(ctx, cudaMemsetAsync(flag, 0, sizeof(int32_t), ctx->stream));
+    launch_build_r1(ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->H.as<double>(), 2.0 / ctx->td, ctx->tc,
+                    rp1, ci1, u64, dg64, u32, dg32, flag, ctx->stream);
+    PFE_TRY(check_launch(ctx, "rank-1 filter operator"));
+    int32_t hbad = 1;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hbad, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->r1_state = hbad ? 0 : 1;
+    ctx->r1_32 = with32;
+    if (hbad) {
+      for (DBuf *b : {&ctx->r1_rp, &ctx->r1_ci, &ctx->r1_u64, &ctx->r1_dg64, &ctx->r1_u32, &ctx->r1_dg32})
+        dbuf_free(*b);
+    }
+  }
   ctx->hs_c = ctx->tc;
   ctx->hs_d = ctx->td;
   ctx->hs_valid = true;
@@ -315,8 +365,9 @@ pfe_status chol_factor(pfe_ctx *ctx, double *G, double *Rinv, int32_t k, bool *s
 // second buffer; *result points to whichever holds Q.  Pass 1: G = Y^T Y, Y R^{-1} -> tmp.
 // Pass 2 only if the Gram matrix of tmp deviates from I by more than 1e-13 (max entry), and
 // a third pass after a shifted factorisation.
-pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result) {
+pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result, bool *shifted_out = nullptr) {
   *result = Y;
+  if (shifted_out) *shifted_out = false;
   if (k <= 0) return PFE_OK;
   cudaStream_t s = ctx->stream;
   RESERVE(double, G, ctx->w_small, (size_t)2 * k * k + 8);
@@ -341,6 +392,7 @@ pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, 
     *result = dst;
     std::swap(src, dst);
   }
+  if (shifted_out) *shifted_out = any_shift;
   return PFE_OK;
 }
 
@@ -662,6 +714,28 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
 }
 
 // ---------------------------------------------------------------- batched filter (host side)
+// fn(i) for i in [0, ns) from up to nthreads host threads (0: min(ns, hardware threads, 16)), each
+// bound to the device; every sample is touched by exactly one thread.
+template <typename F>
+void for_each_sample(int device, int32_t ns, int32_t nthreads, F &&fn) {
+  int32_t nt = nthreads;
+  if (nt <= 0) nt = (int32_t)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+  nt = std::min(nt, ns);
+  if (nt <= 1) {
+    for (int32_t i = 0; i < ns; ++i) fn(i);
+    return;
+  }
+  std::atomic<int32_t> next{0};
+  std::vector<std::thread> pool;
+  pool.reserve(nt);
+  for (int32_t t = 0; t < nt; ++t)
+    pool.emplace_back([&] {
+      cudaSetDevice(device);
+      for (int32_t i = next.fetch_add(1); i < ns; i = next.fetch_add(1)) fn(i);
+    });
+  for (auto &th : pool) th.join();
+}
+
 struct BatchPlan {
   DBuf desc, total;
   std::vector<BatchDesc> h;
@@ -670,6 +744,7 @@ struct BatchPlan {
   int32_t m_max = 0, cpl = 2, blocks = 0;
   cudaStream_t stream = nullptr;  // the batch's own stream (graphs cannot be captured on the legacy stream)
   cudaEvent_t e0 = nullptr, e1 = nullptr, done_ev = nullptr;
+  std::vector<cudaEvent_t> ready;  // per sample: its stream's work before the batched filter
 };
 
 void batch_plan_free(BatchPlan *p) {
@@ -678,6 +753,8 @@ void batch_plan_free(BatchPlan *p) {
   if (p->e0) cudaEventDestroy(p->e0);
   if (p->e1) cudaEventDestroy(p->e1);
   if (p->done_ev) cudaEventDestroy(p->done_ev);
+  for (cudaEvent_t e : p->ready)
+    if (e) cudaEventDestroy(e);
   if (p->stream) {
     cudaStreamSynchronize(p->stream);
     cudaStreamDestroy(p->stream);
@@ -809,6 +886,14 @@ pfe_status batch_filter(pfe_ctx *c0, pfe_ctx **ctxs, int32_t ns, const std::vect
     if (d.m == 0) launch_axpby<double>(ctxs[i]->n, d.k, ctxs[i]->coef[0], st.X, st.ld, 0.0, st.Y, st.ld, ctxs[i]->stream);
   }
   if (items > 0 && p->exec) {
+    // the graph reads every FP64 sample's block: wait for the work queued on the samples' streams
+    if (p->ready.size() != (size_t)ns) p->ready.assign(ns, nullptr);
+    for (int32_t i = 0; i < ns; ++i) {
+      if (p->h[i].k == 0) continue;
+      if (!p->ready[i]) PFE_CUDA_TRY(c0, cudaEventCreateWithFlags(&p->ready[i], cudaEventDisableTiming));
+      PFE_CUDA_TRY(c0, cudaEventRecord(p->ready[i], ctxs[i]->stream));
+      PFE_CUDA_TRY(c0, cudaStreamWaitEvent(s, p->ready[i], 0));
+    }
     PFE_TRY(batch_upload(c0, p, items));
     cudaEventRecord(p->e0, s);
     PFE_CUDA_TRY(c0, cudaGraphLaunch(p->exec, s));
@@ -828,8 +913,8 @@ pfe_status solver_ensure_filter(pfe_ctx *ctx) { return ensure_filter(ctx); }
 pfe_status solver_ensure_hs(pfe_ctx *ctx, bool need32) { return ensure_hs(ctx, need32); }
 pfe_status solver_count(pfe_ctx *ctx) { return count_estimate(ctx); }
 pfe_status solver_window(pfe_ctx *ctx, double *out) { return window_estimate(ctx, out); }
-pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result) {
-  return cholqr2(ctx, Y, tmp, k, ld, result);
+pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result, bool *shifted) {
+  return cholqr2(ctx, Y, tmp, k, ld, result, shifted);
 }
 pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1) {
   return run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k, ld, X, Y, b0, b1, ctx->stream);
@@ -1024,7 +1109,9 @@ void pfe_destroy(pfe_ctx *ctx) {
                   &ctx->w_W, &ctx->w_T0, &ctx->w_T1, &ctx->w_T2, &ctx->w_small, &ctx->w_small2, &ctx->w_red,
                   &ctx->w_idx, &ctx->w_cs_work, &ctx->w_info, &ctx->w_f32a, &ctx->w_f32b, &ctx->w_f32c,
                   &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram,
-                  &ctx->w_bks[0], &ctx->w_bks[1], &ctx->w_bks[2], &ctx->w_bks[3], &ctx->w_bks[4]};
+                  &ctx->w_bks[0], &ctx->w_bks[1], &ctx->w_bks[2], &ctx->w_bks[3], &ctx->w_bks[4],
+                  &ctx->r1_rp, &ctx->r1_ci, &ctx->r1_u64, &ctx->r1_dg64, &ctx->r1_u32, &ctx->r1_dg32,
+                  &ctx->r1_flag};
   for (DBuf *b : bufs) dbuf_free(*b);
   for (int e = 0; e < 4; ++e)
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
@@ -1137,10 +1224,19 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!(v >= 2.0)) return pfe_fail(ctx, PFE_E_ARG, "BASIS_FACTOR must be >= 2");
       ctx->p_basis_factor = v;
       break;
+    case PFE_P_BATCH_THREADS:
+      if (!int_ok(0) || v > 256) return pfe_fail(ctx, PFE_E_ARG, "BATCH_THREADS must be an integer in [0, 256]");
+      ctx->p_batch_threads = (int32_t)v;
+      break;
+    case PFE_P_RANK1:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "RANK1 must be 0 or 1");
+      ctx->p_rank1 = (int)v;
+      if (ctx->p_rank1 && ctx->r1_state == -1) ctx->hs_valid = false;  // build the form with the next filter
+      break;
     case PFE_P_STEP_SHAPE_F64:
     case PFE_P_STEP_SHAPE_F32:
-      if (!(v == -1 || (v >= 0 && v <= 6 && v == std::floor(v))))
-        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..6");
+      if (!(v == -1 || (v >= 0 && v <= 9 && v == std::floor(v))))
+        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..9");
       set_step_variant(key == PFE_P_STEP_SHAPE_F32, (int)v);
       break;
     default:
@@ -1173,6 +1269,8 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_METHOD: *v = ctx->p_method; break;
     case PFE_P_BLOCK: *v = ctx->p_block; break;
     case PFE_P_BASIS_FACTOR: *v = ctx->p_basis_factor; break;
+    case PFE_P_BATCH_THREADS: *v = ctx->p_batch_threads; break;
+    case PFE_P_RANK1: *v = (ctx->p_rank1 && ctx->r1_state == 1) ? 1.0 : 0.0; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;
@@ -1334,11 +1432,12 @@ pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int
   // checkpoint spacing ~ sqrt(m): checkpoints hold (t_j0, t_{j0+1}) for j0 = 0, S, 2S, ...
   const int32_t S = std::max<int32_t>(1, (int32_t)std::ceil(std::sqrt((double)std::max(m, 1))));
   const int32_t nseg = (m + S - 1) / S;
-  // buffers: Xr, Ybr, 3 adjoint vectors, segment buffer of S + 1 vectors, checkpoints 2 * nseg
-  const size_t nvec = 2 + 3 + (size_t)(S + 1) + 2 * (size_t)std::max(nseg, 1);
+  // buffers: Xr, Ybr, adjoint segment of S + 2 vectors, forward segment of S + 1 vectors,
+  // checkpoints 2 * nseg
+  const size_t nvec = 2 + (size_t)(S + 2) + (size_t)(S + 1) + 2 * (size_t)std::max(nseg, 1);
   RESERVE(double, base, ctx->w_ckpt, vec * nvec);
-  double *Xr = base, *Yb = base + vec, *a0 = base + 2 * vec, *a1 = base + 3 * vec, *a2 = base + 4 * vec;
-  double *seg = base + 5 * vec;
+  double *Xr = base, *Yb = base + vec, *aseg = base + 2 * vec;
+  double *seg = aseg + (size_t)(S + 2) * vec;
   double *ck = seg + (size_t)(S + 1) * vec;
   launch_zero<double>(base, (int64_t)(vec * nvec), s);
   launch_colmajor_to_rowmajor<double>(n, k, X, ldx, Xr, ld, s);
@@ -1346,6 +1445,7 @@ pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int
   const Bsr<double> A = bsr_Hs64(ctx);
   const double two_over_d = 2.0 / ctx->td;
   auto tvec = [&](int32_t g, int which) { return ck + ((size_t)2 * g + which) * vec; };
+  auto av = [&](int32_t q) { return aseg + (size_t)q * vec; };
   // forward pass: t_0 .. t_{m-1}, storing (t_j0, t_{j0+1}) at every segment start j0 = g S
   if (m >= 1) {
     double *tp = seg, *tc = seg + vec;  // rolling (t_{j-1}, t_j)
@@ -1365,11 +1465,14 @@ pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int
     if (m - 1 >= 1 && (m - 1) % S == 0) launch_axpby<double>(n, k, 1.0, tc, ld, 0.0, tvec((m - 1) / S, 0), ld, s);
     PFE_TRY(check_launch(ctx, "adjoint forward"));
   }
-  // reverse pass: a_m = g_m ybar; a_j = A a_{j+1} - a_{j+2} + g_j ybar (j >= 1);
-  // a_0 = A a_1 / 2 - a_2 + g_0 ybar; dL/dA += a_{j+1} t_j^T (j >= 1), + a_1 t_0^T / 2.
-  double *an2 = a2, *an1 = a1, *acur = a0;  // a_{j+2}, a_{j+1}, a_j
-  launch_zero<double>(an2, (int64_t)vec, s);
-  launch_axpby<double>(n, k, cf[m], Yb, ld, 0.0, an1, ld, s);  // a_m
+  // reverse pass: a_m = g_m ybar, a_{m+1} = 0; a_j = A a_{j+1} - a_{j+2} + g_j ybar (j >= 1),
+  // a_0 = A a_1 / 2 - a_2 + g_0 ybar; dL/dA += (2/d) a_{j+1} t_j^T (j >= 1) and (1/d) a_1 t_0^T.
+  // Within the segment [j0, j1) the adjoint vectors a_{j0} .. a_{j1+1} sit in av(0) .. av(j1-j0+1),
+  // and the segment's outer products are summed by one launch.
+  if (m >= 1) {
+    const int32_t jl0 = (nseg - 1) * S;
+    launch_axpby<double>(n, k, cf[m], Yb, ld, 0.0, av(m - jl0), ld, s);  // a_m; a_{m+1} is zero
+  }
   for (int32_t g = nseg - 1; g >= 0 && m >= 1; --g) {
     const int32_t j0 = g * S, j1 = std::min(m, j0 + S);  // this segment holds t_j0 .. t_{j1-1}
     // recompute the segment from its checkpoint
@@ -1380,22 +1483,19 @@ pfe_status pfe_filter_adjoint(pfe_ctx *ctx, int32_t m, const double *coeffs, int
       launch_bsr_step<double>(A, MODE_STEP, k, ld, seg + (size_t)(j - j0 - 1) * vec, seg + (size_t)(j - j0 - 2) * vec,
                               out, nullptr, 1.0, -1.0, 0.0, 0.0, s);
     }
-    for (int32_t j = j1 - 1; j >= j0; --j) {
-      const double *tj = seg + (size_t)(j - j0) * vec;
-      // outer products with a_{j+1}
-      launch_outer_accum<double>(A, k, ld, an1, tj, two_over_d * (j >= 1 ? 1.0 : 0.5), vals_bar, s);
-      // a_j
-      if (j >= 1)
-        launch_bsr_step<double>(A, MODE_ADJ, k, ld, an1, an2, acur, Yb, 1.0, -1.0, cf[j], 0.0, s);
-      else
-        launch_bsr_step<double>(A, MODE_ADJ, k, ld, an1, an2, acur, Yb, 0.5, -1.0, cf[0], 0.0, s);
-      double *t = an2;
-      an2 = an1;
-      an1 = acur;
-      acur = t;
+    for (int32_t j = j1 - 1; j >= j0; --j)
+      launch_bsr_step<double>(A, MODE_ADJ, k, ld, av(j - j0 + 1), av(j - j0 + 2), av(j - j0), Yb, j >= 1 ? 1.0 : 0.5,
+                              -1.0, cf[j], 0.0, s);
+    // sum_{j in [j0, j1)} alpha_j a_{j+1} t_j^T over the stored blocks
+    launch_outer_accum_seg(A, ctx->nnzb, k, ld, j1 - j0, (int64_t)vec, av(1), seg, two_over_d * (j0 == 0 ? 0.5 : 1.0),
+                           two_over_d, vals_bar, s);
+    if (g > 0) {  // (a_{j0}, a_{j0+1}) become the next segment's (a_{j1'}, a_{j1'+1}), j1' = j0
+      launch_axpby<double>(n, k, 1.0, av(1), ld, 0.0, av(S + 1), ld, s);
+      launch_axpby<double>(n, k, 1.0, av(0), ld, 0.0, av(S), ld, s);
     }
   }
-  // an1 now holds a_0 (or a_m = g_0 ybar for m == 0)
+  double *an1 = av(0);  // a_0
+  // a_0 = g_0 ybar for m == 0
   if (m == 0) launch_axpby<double>(n, k, cf[0], Yb, ld, 0.0, an1, ld, s);
   launch_rowmajor_to_colmajor<double>(n, k, an1, ld, Xbar, ldxb, s);
   return check_launch(ctx, "filter_adjoint");
@@ -1424,8 +1524,9 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     if (ctxs[i]->device != c0->device) return pfe_fail(c0, PFE_E_ARG, "batch contexts must share one device");
   if (cudaSetDevice(c0->device) != cudaSuccess) return pfe_fail(c0, PFE_E_CUDA, "cudaSetDevice failed");
   std::vector<pfe_status> status(nsamples, PFE_OK);
+  const int32_t nthreads = c0->p_batch_threads;
   // set-up of every sample (filter design, width, buffers, start block)
-  for (int32_t i = 0; i < nsamples; ++i) status[i] = solve_setup(ctxs[i]);
+  for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) { status[i] = solve_setup(ctxs[i]); });
   BatchPlan plan;
   pfe_status bst = batch_plan_init(c0, ctxs, nsamples, status, &plan);
   if (bst != PFE_OK) {
@@ -1441,11 +1542,11 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
       if (status[i] == PFE_OK && !ctxs[i]->solve.done) any = true;
     if (!any) break;
     // 1. filter: one batched replay for the FP64 samples, the single-context path for FP32 ones
-    for (int32_t i = 0; i < nsamples; ++i) {
+    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) {
       SolveState &st = ctxs[i]->solve;
-      if (status[i] != PFE_OK || st.done || st.use64) continue;
+      if (status[i] != PFE_OK || st.done || st.use64) return;
       status[i] = solve_filter(ctxs[i]);
-    }
+    });
     float ms = 0.f;
     bst = batch_filter(c0, ctxs, nsamples, status, &plan, &ms);
     if (bst != PFE_OK) {
@@ -1455,12 +1556,12 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     t_batch_filter += ms * 1e-3;
     ++batch_replays;
     // 2. everything after the filter, per sample (its own stream waits for the batched filter)
-    for (int32_t i = 0; i < nsamples; ++i) {
+    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) {
       SolveState &st = ctxs[i]->solve;
-      if (status[i] != PFE_OK || st.done) continue;
+      if (status[i] != PFE_OK || st.done) return;
       cudaStreamWaitEvent(ctxs[i]->stream, plan.done_ev, 0);
       status[i] = solve_after_filter(ctxs[i]);
-    }
+    });
   }
   batch_plan_free(&plan);
   pfe_status first = PFE_OK;

@@ -26,7 +26,8 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--degree", type=int, default=8)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--shape", type=int, default=-1, help="kernel shape 0..6, -1 = autotuned")
+    ap.add_argument("--shape", type=int, default=-1, help="kernel shape 0..9, -1 = autotuned")
+    ap.add_argument("--rank1", type=int, default=1, help="1: the rank-1 form of the spring network when it has one")
     ap.add_argument("--adjoint", action="store_true", help="time pfe_filter_adjoint (FP64) at this degree instead")
     a = ap.parse_args()
     torch.cuda.set_device(0)
@@ -35,6 +36,7 @@ def main():
     ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
     try:
         pfe.pfe_set_param(ctx, pfe.PFE_P_STEP_SHAPE_F64 if a.dtype == "f64" else pfe.PFE_P_STEP_SHAPE_F32, a.shape)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_RANK1, a.rank1)
         pfe.pfe_estimate(ctx)
         tdt = torch.float64 if a.dtype == "f64" else torch.float32
         dt = pfe.PFE_F64 if a.dtype == "f64" else pfe.PFE_F32
@@ -45,6 +47,10 @@ def main():
         nnzb = ci.size
         step_bytes = -(-a.k // kt) * (nnzb * (9 * s + 4) + 4 * (g.n_atoms + 1)) + 5 * g.n * a.k * s
         step_flops = 18 * nnzb * a.k + 6 * g.n * a.k
+        noff = nnzb - g.n_atoms
+        # the rank-1 form: 3 values and 6 FMAs per off-diagonal block and column, full diagonal blocks
+        r1_bytes = -(-a.k // kt) * (noff * (3 * s + 4) + g.n_atoms * 6 * s + 4 * (g.n_atoms + 1)) + 5 * g.n * a.k * s
+        r1_flops = 12 * noff * a.k + 18 * g.n_atoms * a.k + 6 * g.n * a.k
         if a.adjoint:
             coef = np.ones(a.degree + 1) / (a.degree + 1)
             Xb = torch.empty_like(X)
@@ -78,10 +84,13 @@ def main():
                 torch.cuda.synchronize()
                 best.append(e0.elapsed_time(e1) / 1e3)
             times[m] = best
+        r1 = pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1) == 1 and (a.shape < 0 or a.shape >= 7)
+        byts, flops = (r1_bytes, r1_flops) if r1 else (step_bytes, step_flops)
         for r in range(a.reps):
             per = (times[a.degree + 1][r] - times[1][r]) / a.degree
-            print(json.dumps({"n_atoms": g.n_atoms, "k": a.k, "dtype": a.dtype, "shape": a.shape, "s_per_step": per,
-                              "alg_gbs": step_bytes / per / 1e9, "alg_gflops": step_flops / per / 1e9}), flush=True)
+            print(json.dumps({"n_atoms": g.n_atoms, "k": a.k, "dtype": a.dtype, "shape": a.shape,
+                              "form": "rank1" if r1 else "bsr", "s_per_step": per,
+                              "alg_gbs": byts / per / 1e9, "alg_gflops": flops / per / 1e9}), flush=True)
     finally:
         pfe.pfe_destroy(ctx)
 

@@ -64,8 +64,10 @@ def cluster_angles_ok(H, lam, V, w_all, U_sel, w_sel, lmax):
         others = np.concatenate([w_all[w_all < w_sel[i] - 1e-6 * lmax], w_all[w_all > w_sel[j - 1] + 1e-6 * lmax]])
         gap = np.min(np.minimum(np.abs(others - w_sel[i]), np.abs(others - w_sel[j - 1])))
         R = H.matmul(V[:, i:j]) - V[:, i:j] * lam[i:j]
-        s = np.linalg.svd(U_sel[:, i:j].T @ V[:, i:j], compute_uv=False)
-        sin_t = np.sqrt(max(0.0, 1.0 - np.min(s) ** 2))
+        # sine of the largest principal angle as ||(I - U U^T) V||_2, accurate to rounding (the
+        # form sqrt(1 - cos^2) cannot resolve angles below ~1e-8)
+        Uc, Vc = U_sel[:, i:j], V[:, i:j]
+        sin_t = np.linalg.norm(Vc - Uc @ (Uc.T @ Vc), 2)
         if sin_t > 2.0 * np.linalg.norm(R) / gap + 1e-12:
             return False
         i = j
@@ -90,9 +92,10 @@ def test_filter_fp64_parity(N, seed, k, m):
         pfe.pfe_destroy(ctx)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_filter_every_kernel_shape(shape):
-    """Each kernel shape of the fused step (forced instead of autotuned), FP64 and FP32, ragged k."""
+    """Each kernel shape of the fused step (forced instead of autotuned), FP64 and FP32, ragged k;
+    shapes 7-9 run on the rank-1 form of the spring network's operator."""
     g = glassgen.generate(333, 13)
     ctx, _ = make_ctx(g, LAMBDA_MAX=0.25)
     try:
@@ -106,8 +109,75 @@ def test_filter_every_kernel_shape(shape):
                 ref = oracle.cheb_filter(ref_c, 0.125, 0.125, coef, X)
                 assert np.max(np.abs(Y - ref)) <= tol * np.abs(X).max() * np.abs(coef).sum(), (dt, k)
             pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), -1)
+        assert pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1) == 1  # the spring network has the rank-1 form
     finally:
         pfe.pfe_destroy(ctx)
+
+
+def _bsr_to_oracle_csr(rp, ci, vals):
+    """Scalar CSR (oracle) of a BSR matrix with 3x3 row-major blocks."""
+    N = rp.size - 1
+    rows = [[] for _ in range(3 * N)]
+    for i in range(N):
+        for p in range(rp[i], rp[i + 1]):
+            for r in range(3):
+                for c in range(3):
+                    rows[3 * i + r].append((3 * ci[p] + c, vals[9 * p + 3 * r + c]))
+    rpc = np.zeros(3 * N + 1, np.int32)
+    cic, vc = [], []
+    for r, row in enumerate(rows):
+        row.sort()
+        rpc[r + 1] = rpc[r] + len(row)
+        cic += [c for c, _ in row]
+        vc += [v for _, v in row]
+    return oracle.csr_from_arrays(rpc, np.array(cic, np.int32), np.array(vc))
+
+
+@pytest.mark.parametrize("rank1", [0, 1])
+def test_general_blocks_use_the_full_form(rank1):
+    """Off-diagonal blocks that are not -k r r^T (a symmetric perturbation of a spring network):
+    the rank-1 form is refused and the filter and the solve run on the full 3x3 blocks."""
+    g = glassgen.generate(120, 21)
+    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    rng = np.random.default_rng(5)
+    H = vals.copy()
+    N = g.n_atoms
+    for i in range(N):  # mass weighting here; the context gets H directly (masses None)
+        for p in range(rp[i], rp[i + 1]):
+            H[9 * p:9 * p + 9] /= np.sqrt(g.mass[i] * g.mass[ci[p]])
+    blk = {(i, int(ci[p])): p for i in range(N) for p in range(rp[i], rp[i + 1])}
+    for (i, j), p in blk.items():
+        if i < j:
+            S = rng.standard_normal((3, 3)) * 1e-3
+            S = S + S.T
+            H[9 * p:9 * p + 9] += S.ravel()
+            q = blk[(j, i)]
+            H[9 * q:9 * q + 9] += S.T.ravel()
+    ctx = pfe.pfe_create(N, rp, ci, H, None)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_RANK1, rank1)
+        lmax, _ = pfe.pfe_estimate(ctx)
+        coef = oracle.filter_coeffs(-0.95, -0.9, 0.02, 30, "none")
+        X = np.random.default_rng(2).standard_normal((g.n, 9))
+        Y = filter_gpu(ctx, coef, X)
+        assert pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1) == 0
+        Hc = _bsr_to_oracle_csr(rp, ci, H)
+        ref = oracle.cheb_filter(Hc, 0.5 * lmax, 0.5 * lmax, coef, X)
+        assert np.max(np.abs(Y - ref)) <= 1e-11 * np.abs(X).max() * np.abs(coef).sum()
+        lo, hi = 0.05 * lmax, 0.12 * lmax
+        pfe.pfe_set_interval(ctx, lo, hi)
+        nf, _ = pfe.pfe_solve(ctx)
+        lam, _, _ = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
+        w, _, _ = oracle.exact_interval(Hc, lo, hi)
+        assert nf == w.size and np.allclose(lam, w, rtol=1e-10, atol=0)
+    finally:
+        pfe.pfe_destroy(ctx)
+
+
+@pytest.mark.parametrize("rank1", [0, 1])
+def test_solve_with_and_without_rank1_form(rank1):
+    st = _solve_and_check(glassgen.generate(300, 5), 0.05, 0.12, RANK1=rank1)
+    assert st["iterations"] >= 2
 
 
 def test_filter_first_step_is_transformed_hessian():
@@ -260,15 +330,17 @@ def test_solve_capacity_error():
         pfe.pfe_destroy(ctx)
 
 
-def test_solve_batch_equals_solo():
+@pytest.mark.parametrize("threads", [0, 1, 3])
+def test_solve_batch_equals_solo(threads):
     """Batched lockstep solve (one persistent filter launch per step over all samples, replayed from
-    a CUDA graph): every sample matches the exact interval eigenpairs and its own solo solve."""
+    a CUDA graph; the samples' dense steps from `threads` host threads, 0 = automatic): every sample
+    matches the exact interval eigenpairs and its own solo solve."""
     sizes = (150, 420, 180, 300, 95)
     gs = [glassgen.generate(n, glassgen.subseed(3, i)) for i, n in enumerate(sizes)]
     ctxs = []
     try:
         for g in gs:
-            ctx, _ = make_ctx(g)
+            ctx, _ = make_ctx(g, BATCH_THREADS=threads)
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.15 * lmax)
             ctxs.append(ctx)
@@ -333,14 +405,16 @@ def _bsr_to_csr_index(rp_b, ci_b, rp_c):
     return idx
 
 
-def test_adjoint_and_chain_parity():
+@pytest.mark.parametrize("m,k", [(0, 2), (1, 3), (2, 4), (14, 3), (16, 8), (37, 11)])
+def test_adjoint_and_chain_parity(m, k):
+    """Degrees that give one, several, exactly filled and ragged checkpoint segments (S = ceil(sqrt m));
+    odd and even block widths."""
     g = glassgen.generate(90, 6)
     ctx, (rp, ci, vals) = make_ctx(g, LAMBDA_MAX=0.2)
     try:
         c = d = 0.1
-        coef = oracle.filter_coeffs(-0.9, -0.8, 0.03, 14, "jackson")
-        rng = np.random.default_rng(4)
-        k = 3
+        coef = oracle.filter_coeffs(-0.9, -0.8, 0.03, m, "jackson")
+        rng = np.random.default_rng(4 + m)
         X = rng.standard_normal((g.n, k))
         Yb = rng.standard_normal((g.n, k))
         Xd, Ybd = dev_colmajor(X), dev_colmajor(Yb)
