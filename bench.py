@@ -40,9 +40,11 @@ WORKLOADS = {
 DEFAULT = "glass-n100k-fp64"
 
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
-# DRAM traffic / algorithmic bytes of the fused step, from one ncu capture per type (N = 100,000;
-# k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md, filter_step_f32_n100k.md)
-TRAFFIC_RATIO = {8: 872.490752 / 854.171476, 4: 830.966784 / 813.542884}
+# DRAM traffic / algorithmic bytes of the fused step on full 3x3 blocks, from one ncu capture per
+# type (N = 100,000; k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md,
+# filter_step_f32_n100k.md).  The rank-1 kernel has no capture yet: its traffic is reported null.
+TRAFFIC_RATIO = {("bsr", 8): 872.490752 / 854.171476, ("bsr", 4): 830.966784 / 813.542884}
+R1_SHAPES = (7, 8, 9)  # kernel shapes of the fused step that run on the rank-1 form
 
 
 def peaks():
@@ -55,13 +57,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def filter_work(n_atoms, nnzb, k, vec_bytes, val_bytes):
-    """Algorithmic bytes and flops of one fused Chebyshev step on k columns (one launch)."""
+def filter_work(n_atoms, nnzb, k, vec_bytes, val_bytes, rank1=False):
+    """Algorithmic bytes and flops of one fused Chebyshev step on k columns (one launch).
+    Full 3x3 blocks: 9 values and 9 FMAs per block and column.  Rank-1 form of a spring network:
+    3 values and 6 FMAs per off-diagonal block and column, a full symmetric diagonal block (6 values,
+    9 FMAs) per atom."""
     n = 3 * n_atoms
     kt = 128 if vec_bytes == 4 else 64  # columns per warp (CPL x 32)
     tiles = -(-k // kt)
-    byts = tiles * (nnzb * (9 * val_bytes + 4) + 4 * (n_atoms + 1)) + 5 * n * k * vec_bytes
-    flops = 18 * nnzb * k + 6 * n * k
+    vec = 5 * n * k * vec_bytes  # gather t_j, read t_{j-1}, write t_{j+1}, read and write y
+    if rank1:
+        noff = nnzb - n_atoms
+        byts = tiles * (noff * (3 * val_bytes + 4) + n_atoms * 6 * val_bytes + 4 * (n_atoms + 1)) + vec
+        flops = 12 * noff * k + 18 * n_atoms * k + 6 * n * k
+    else:
+        byts = tiles * (nnzb * (9 * val_bytes + 4) + 4 * (n_atoms + 1)) + vec
+        flops = 18 * nnzb * k + 6 * n * k
     return byts, flops
 
 
@@ -133,6 +144,7 @@ def one_step(pfe, torch, g, rp, ci, vals, wl, ev):
     ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
     try:
         pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, wl["precision"])
+        pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, wl.get("method", 0))
         torch.cuda.synchronize()
         ev[1].record()
         lmax, _ = pfe.pfe_estimate(ctx)
@@ -272,26 +284,32 @@ def run_native(args, wl):
     nnzb = int(ci.size)
     hbm, hbm_src = peaks()
     if last["filter_col_steps"] > 0:
+        r1 = last["filter_shape_f64"] in R1_SHAPES
+        form = "rank1" if r1 else "bsr"
         secs64 = last["seconds_filter"] - last["seconds_filter_f32"]
-        _, fl = filter_work(g.n_atoms, nnzb, 1, 8, 8)
+        _, fl = filter_work(g.n_atoms, nnzb, 1, 8, 8, r1)
         flops = fl * last["filter_col_steps"]
         achieved = flops / secs64 / 1e12
-        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 8, 8)
+        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 8, 8, r1)
         avg_k = last["filter_col_steps"] / max(last["filter_launches"], 1)
-        bl, _ = filter_work(g.n_atoms, nnzb, int(round(avg_k)), 8, 8)
-        roof = {"bound": "alu", "kernel": "k_bsr_step<double> (fused Chebyshev step)", "achieved": achieved,
+        bl, _ = filter_work(g.n_atoms, nnzb, int(round(avg_k)), 8, 8, r1)
+        ratio = TRAFFIC_RATIO.get((form, 8))
+        roof = {"bound": "alu", "kernel": ("k_r1_step<double>" if r1 else "k_bsr_step<double>") +
+                " (fused Chebyshev step, shape %d)" % last["filter_shape_f64"], "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_RATIO[8] * bl, "traffic_note": "bytes per average launch: algorithmic x the "
-                "ncu-measured DRAM/algorithmic ratio of the k = 64 capture",
+                "traffic": ratio * bl if ratio else None,
+                "traffic_note": ("bytes per average launch: algorithmic x the ncu-measured DRAM/algorithmic "
+                                 "ratio of the k = 64 capture") if ratio else "no ncu capture of this kernel yet",
                 "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
                 "filter_gbs_fp64": (b1 / last["width"]) * last["filter_col_steps"] / secs64 / 1e9,
-                "launches": last["filter_launches"]}
+                "launches": last["filter_launches"], "operator_form": form}
     else:
+        r1 = last["filter_shape_f32"] in R1_SHAPES
         secs32 = last["seconds_filter_f32"]
-        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 4, 4)
+        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 4, 4, r1)
         gbs = (b1 / last["width"]) * last["filter_col_steps_f32"] / secs32 / 1e9
-        roof = {"bound": "hbm", "kernel": "k_bsr_step<float>", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                "frac": gbs / hbm, "traffic": None, "peak_source": hbm_src}
+        roof = {"bound": "hbm", "kernel": "k_r1_step<float>" if r1 else "k_bsr_step<float>", "achieved": gbs,
+                "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_source": hbm_src}
     line = {
         "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * solve_s, "higher_is_better": False,
@@ -316,13 +334,25 @@ def run_native(args, wl):
         wm = dict(wl, precision=1)  # the FP64 warm-up steps above also warmed this path's set-up
         e = evs()
         sm = one_step(pfe, torch, g, rp, ci, vals, wm, e)
-        b1, _ = filter_work(g.n_atoms, nnzb, sm["width"], 4, 4)
+        b1, _ = filter_work(g.n_atoms, nnzb, sm["width"], 4, 4, sm["filter_shape_f32"] in R1_SHAPES)
         gbs32 = (b1 / sm["width"]) * sm["filter_col_steps_f32"] / max(sm["seconds_filter_f32"], 1e-12) / 1e9
         line["mixed"] = {"value": e[1].elapsed_time(e[2]) / 1e3, "unit": "s", "fp64_sweeps": sm["fp64_sweeps"],
                          "iterations": sm["iterations"], "n_found": sm["n_found"],
                          "max_rel_residual": sm["max_rel_residual"],
                          "filter_f32": {"achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
-                                        "peak_source": hbm_src}}
+                                        "peak_source": hbm_src, "shape": sm["filter_shape_f32"]}}
+    if rank == 0 and args.block_lanczos and wl["precision"] == 0:
+        wb = dict(wl, method=1)
+        e = evs()
+        sb = one_step(pfe, torch, g, rp, ci, vals, wb, e)
+        line["block_lanczos"] = {"value": e[1].elapsed_time(e[2]) / 1e3, "unit": "s", "n_found": sb["n_found"],
+                                 "matvecs": sb["matvecs"], "restarts": sb["restarts"], "basis": sb["basis"],
+                                 "block": sb["width"], "max_rel_residual": sb["max_rel_residual"],
+                                 "breakdown_s": {"filter": sb["seconds_filter"], "orth": sb["seconds_orth"],
+                                                 "rr": sb["seconds_rr"]},
+                                 "note": "thick-restart block Lanczos on p(Ht), then Rayleigh-Ritz with H "
+                                         "(the paper's block Krylov-Schur solver); timed once after the "
+                                         "subspace-iteration steps"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -338,6 +368,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-block-lanczos", dest="block_lanczos", action="store_false")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -91,7 +91,7 @@ enum {
                                Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),
                                FP64 only */
   PFE_P_BLOCK = 22,         /* block size of METHOD 1 (default 64) */
-  PFE_P_BASIS_FACTOR = 23,  /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 3, Sec. 3) */
+  PFE_P_BASIS_FACTOR = 23,  /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 2; >= 2) */
   PFE_P_BATCH_THREADS = 24, /* pfe_solve_batch, read from the first context: host threads that run the
                                samples' set-up and dense steps concurrently, each sample on its own
                                stream (0 = automatic: min(samples, hardware threads, 16); 1 = serial) */
@@ -193,6 +193,9 @@ typedef struct {
   int64_t batch_replays;       /* pfe_solve_batch: replays of the captured batched-filter graph */
   int32_t restarts;            /* METHOD 1: thick restarts */
   int32_t basis;               /* METHOD 1: maximal basis size */
+  int32_t filter_shape_f64;    /* kernel shape of the last FP64 filter step (PFE_P_STEP_SHAPE_F64 numbering;
+                                  7-9: the rank-1 form), -1 if none ran */
+  int32_t filter_shape_f32;    /* the same for the FP32 filter step */
 } pfe_stats;
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 
@@ -260,6 +263,30 @@ pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeff
  * In the stats of every sample seconds_filter is the batch's shared filter time.
  * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
+
+/* ---------------------------------------------------------------------------------------
+ * Analysis of the computed modes (Sec. 4.3).  A mode q is read as N 3-vectors q_i, the three
+ * dof rows of atom i; both calls work on the context's found eigenvectors, on the device, in the
+ * order of pfe_get_eigenpairs.  PFE_E_STATE without solve results; PFE_E_CAPACITY if cap < n_found.
+ * ------------------------------------------------------------------------------------- */
+
+/* Participation ratio of eq. (PR_def), normalised by the atom count so that a mode spread evenly
+ * over all atoms gives 1, a single-atom mode 1/N and a plane wave 2/3:
+ *     pr[s] = (sum_i |q_i|^2)^2 / (N sum_i |q_i|^4).
+ * pr: host array of cap doubles. */
+pfe_status pfe_participation_ratio(pfe_ctx *ctx, int32_t cap, double *pr);
+
+/* Plane-wave content of each mode for nk wave vectors (the identification of sound modes by
+ * wave vector k = 2 pi (m, n, l) / L and polarisation in Sec. 4.3).  With
+ * A_d = sum_i q_{i,d} exp(i k . r_i) (d = x, y, z), k^ = k / |k|:
+ *     out[2 (s nk + w)]     = (2/N) |k^ . A|^2 / |q|^2            (longitudinal)
+ *     out[2 (s nk + w) + 1] = (2/N) (|A|^2 - |k^ . A|^2) / |q|^2  (transverse, both polarisations)
+ * i.e. the weight of q on the plane waves sqrt(2/N) zeta sin(k . r_i), sqrt(2/N) zeta cos(k . r_i);
+ * a plane wave of an allowed k gives 1 in its polarisation.  pos: host, 3N atom positions in the
+ * atom order of H (any length unit); kvec: host, 3 nk components in the inverse unit, each nonzero
+ * (PFE_E_ARG otherwise); out: host, 2 cap nk doubles. */
+pfe_status pfe_plane_wave_content(pfe_ctx *ctx, const double *pos, int32_t nk, const double *kvec, int32_t cap,
+                                  double *out);
 
 #ifdef __cplusplus
 }

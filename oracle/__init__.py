@@ -60,6 +60,8 @@ def _load():
         _sig(lib, "or_csr_from_springs", _P, [_I32, _I64, _P, _P, _P, _P, _P])
         _sig(lib, "or_spmm", None, [_P, _I32, _P, _I64, _P, _I64])
         _sig(lib, "or_residuals", None, [_P, _I32, _P, _P, _I64, _P])
+        _sig(lib, "or_participation_ratio", None, [_I64, _I32, _P, _I64, _P])
+        _sig(lib, "or_plane_wave_content", None, [_I64, _I32, _P, _I64, _P, _I32, _P, _P])
         _sig(lib, "or_pq_coeffs", None, [_D, _D, _D, _I32, _P])
         _sig(lib, "or_chi_coeffs", None, [_D, _D, _I32, _P])
         _sig(lib, "or_damping", None, [ctypes.c_int, _I32, _P])
@@ -373,3 +375,22 @@ def exact_interval(H: CSR, a, b):
     w, V = np.linalg.eigh(H.dense())
     sel = (w >= a) & (w <= b)
     return w[sel], V[:, sel], w
+
+
+def participation_ratio(V) -> np.ndarray:
+    """Normalised participation ratio of each column (Sec. 4.3, eq. (PR_def) divided by N)."""
+    V = _fortran(np.asarray(V, np.float64).reshape(np.shape(V)[0], -1))
+    pr = np.zeros(V.shape[1])
+    _load().or_participation_ratio(V.shape[0] // 3, V.shape[1], _ptr(V), V.shape[0], _ptr(pr))
+    return pr
+
+
+def plane_wave_content(V, pos, kvecs) -> np.ndarray:
+    """(k, nk, 2): longitudinal and transverse plane-wave content of each column (Sec. 4.3)."""
+    V = _fortran(np.asarray(V, np.float64).reshape(np.shape(V)[0], -1))
+    pos = _f64(np.asarray(pos).reshape(-1))
+    kv = _f64(np.asarray(kvecs).reshape(-1, 3))
+    out = np.zeros((V.shape[1], kv.shape[0], 2))
+    _load().or_plane_wave_content(V.shape[0] // 3, V.shape[1], _ptr(V), V.shape[0], _ptr(pos), kv.shape[0], _ptr(kv),
+                                  _ptr(out))
+    return out

@@ -1249,3 +1249,64 @@ int or_bks_solve(const or_csr *H, double a, double b, double lmin, double lmax, 
   free(V); free(OV); free(Y); free(OY); free(T); free(S); free(th); free(rr); free(h); free(ord);
   return status;
 }
+
+/* ======================================================================================
+ * Analysis of the computed modes, Sec. 4.3
+ * ==================================================================================== */
+
+/* Participation ratio, eq. (PR_def): PR = 1 / sum_i |q_i|^4 for a mode of unit 2-norm, q_i the
+ * 3-vector of atom i.  The paper then reads PR = 1 for |q_i| = 1/sqrt(N) and PR = 1/N for a
+ * single atom, which is the printed formula divided by N; this routine returns that normalised
+ * value, with the unit-norm assumption written out: (sum |q_i|^2)^2 / (N sum |q_i|^4).
+ * V: n x k column-major (n = 3 n_atoms), ld ldv. */
+void or_participation_ratio(int64_t n_atoms, int32_t k, const double *V, int64_t ldv, double *pr) {
+  for (int32_t c = 0; c < k; ++c) {
+    const double *q = V + (int64_t)c * ldv;
+    double s2 = 0.0, s4 = 0.0;
+    for (int64_t i = 0; i < n_atoms; ++i) {
+      double w = q[3 * i] * q[3 * i] + q[3 * i + 1] * q[3 * i + 1] + q[3 * i + 2] * q[3 * i + 2];
+      s2 += w;
+      s4 += w * w;
+    }
+    pr[c] = (s4 > 0.0) ? s2 * s2 / ((double)n_atoms * s4) : 0.0;
+  }
+}
+
+/* Plane-wave content of each mode for wave vectors kvec[w] (Sec. 4.3: a plane wave of wave
+ * vector k and polarisation zeta is q_i = sqrt(2/N) zeta sin(k . r_i), r_i the atom position):
+ * the squared projections onto sqrt(2/N) zeta sin(k . r_i) and sqrt(2/N) zeta cos(k . r_i), summed
+ * over both and over the polarisations along k (out[.. 0]) and across k (out[.. 1]), divided by
+ * |q|^2.  Written with A_d = sum_i q_{i,d} (cos + i sin)(k . r_i):
+ *   longitudinal (2/N) |khat . A|^2 / |q|^2, transverse (2/N) (|A|^2 - |khat . A|^2) / |q|^2.
+ * out[(c * nk + w) * 2 + {0, 1}].  pos: 3 n_atoms; kvec: 3 nk, each nonzero. */
+void or_plane_wave_content(int64_t n_atoms, int32_t k, const double *V, int64_t ldv, const double *pos, int32_t nk,
+                           const double *kvec, double *out) {
+  for (int32_t c = 0; c < k; ++c) {
+    const double *q = V + (int64_t)c * ldv;
+    double nrm2 = 0.0;
+    for (int64_t i = 0; i < 3 * n_atoms; ++i) nrm2 += q[i] * q[i];
+    for (int32_t w = 0; w < nk; ++w) {
+      const double *kv = kvec + 3 * w;
+      double re[3] = {0.0, 0.0, 0.0}, im[3] = {0.0, 0.0, 0.0};
+      for (int64_t i = 0; i < n_atoms; ++i) {
+        double ph = kv[0] * pos[3 * i] + kv[1] * pos[3 * i + 1] + kv[2] * pos[3 * i + 2];
+        double cs = cos(ph), sn = sin(ph);
+        for (int d = 0; d < 3; ++d) {
+          re[d] += q[3 * i + d] * cs;
+          im[d] += q[3 * i + d] * sn;
+        }
+      }
+      double kn = sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+      double lre = 0.0, lim = 0.0, tot = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        lre += kv[d] / kn * re[d];
+        lim += kv[d] / kn * im[d];
+        tot += re[d] * re[d] + im[d] * im[d];
+      }
+      double l2 = lre * lre + lim * lim;
+      double sc = (nrm2 > 0.0) ? 2.0 / ((double)n_atoms * nrm2) : 0.0;
+      out[((int64_t)c * nk + w) * 2] = sc * l2;
+      out[((int64_t)c * nk + w) * 2 + 1] = sc * (tot - l2);
+    }
+  }
+}

@@ -39,7 +39,8 @@ PFE_P_METHOD, PFE_P_BLOCK, PFE_P_BASIS_FACTOR, PFE_P_BATCH_THREADS, PFE_P_RANK1 
 EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", "pfe_set_param",
            "pfe_get_param", "pfe_set_interval", "pfe_estimate", "pfe_get_filter", "pfe_solve",
            "pfe_get_eigenpairs", "pfe_get_stats", "pfe_filter_apply", "pfe_filter_adjoint",
-           "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc")
+           "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc", "pfe_participation_ratio",
+           "pfe_plane_wave_content")
 
 
 class PfeError(RuntimeError):
@@ -58,7 +59,8 @@ class PfeStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("filter_launches", ctypes.c_int64),
                 ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
                 ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64),
-                ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32)]
+                ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32), ("filter_shape_f64", ctypes.c_int32),
+                ("filter_shape_f32", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -95,6 +97,8 @@ def load(path: str | None = None):
         "pfe_chain_springs": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P]),
         "pfe_solve_batch": (ctypes.c_int, [_P, _I32, _P]),
         "pfe_filter_apply_noalloc": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _I64, _P]),
+        "pfe_participation_ratio": (ctypes.c_int, [_P, _I32, _P]),
+        "pfe_plane_wave_content": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -289,3 +293,21 @@ def pfe_filter_apply_noalloc(ctx, m, coeffs, k, X, ldx, Y, ldy, stream=None):
     st = load().pfe_filter_apply_noalloc(ctx, int(m), coeffs.ctypes.data, int(k), _dptr(X), int(ldx), _dptr(Y),
                                          int(ldy), _stream(stream))
     _check(st, ctx)
+
+
+def pfe_participation_ratio(ctx, cap):
+    """Participation ratio (normalised by N) of each found eigenvector, in eigenpair order."""
+    pr = np.zeros(max(int(cap), 0))
+    _check(load().pfe_participation_ratio(ctx, int(cap), pr.ctypes.data), ctx)
+    return pr
+
+
+def pfe_plane_wave_content(ctx, pos, kvecs, cap):
+    """(cap, nk, 2) array: longitudinal and transverse plane-wave content of each found eigenvector."""
+    pos = _host(pos, np.float64).reshape(-1)
+    kv = _host(kvecs, np.float64).reshape(-1, 3)
+    out = np.zeros((max(int(cap), 0), kv.shape[0], 2))
+    st = load().pfe_plane_wave_content(ctx, pos.ctypes.data, kv.shape[0], np.ascontiguousarray(kv).ctypes.data,
+                                       int(cap), out.ctypes.data)
+    _check(st, ctx)
+    return out

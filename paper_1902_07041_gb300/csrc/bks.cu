@@ -330,6 +330,8 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   o.kernel_launches = launch_count() - ctx->launch_base;
   o.filter_launches = f_launch;
   o.filter_col_steps = f_cols;
+  o.filter_shape_f64 = f_cols > 0 ? step_last_variant(0) : -1;
+  o.filter_shape_f32 = -1;
   o.seconds_total = solver_now() - t_start;
   if (n_found) *n_found = nf;
   if (result == PFE_E_CAPACITY) return pfe_fail(ctx, result, "the wanted Ritz values fill the basis: raise BASIS_FACTOR");

@@ -8,6 +8,7 @@
 // 32 * CPL columns); each lane owns CPL adjacent columns and keeps 3 x CPL accumulators.
 // Block values and column indices are warp-uniform loads (served as L1 broadcasts); every
 // 3x3 block is read once per column chunk.
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -311,6 +312,15 @@ void set_step_variant(int is_float, int variant) { g_forced[is_float ? 1 : 0] = 
 int step_variant(int is_float) { return g_forced[is_float ? 1 : 0]; }
 
 namespace {
+std::atomic<int> g_last_variant[2] = {{-1}, {-1}};
+}
+int step_last_variant(int is_float) { return g_last_variant[is_float ? 1 : 0].load(); }
+void reset_step_last_variant() {
+  g_last_variant[0].store(-1);
+  g_last_variant[1].store(-1);
+}
+
+namespace {
 template <typename T>
 int cpl_for(int32_t k, int64_t ld, bool al16, bool al8);
 template <>
@@ -399,6 +409,7 @@ void launch_bsr_step<double>(const Bsr<double> &A, int mode, int32_t k, int64_t 
   const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
   const int cpl = cpl_for<double>(k, ld, al16, false);
   const int v = pick_variant(0, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
+  if (mode == MODE_FIRST || mode == MODE_STEP) g_last_variant[0].store((v >= kVariants && !A.u) ? 0 : v);
   dispatch_cpl<double>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
@@ -410,6 +421,7 @@ void launch_bsr_step<float>(const Bsr<float> &A, int mode, int32_t k, int64_t ld
   const bool al8 = aligned(X, 8) && aligned(W, 8) && aligned(Z, 8) && aligned(Y, 8);
   const int cpl = cpl_for<float>(k, ld, al16, al8);
   const int v = pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
+  if (mode == MODE_FIRST || mode == MODE_STEP) g_last_variant[1].store((v >= kVariants && !A.u) ? 0 : v);
   dispatch_cpl<float>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 

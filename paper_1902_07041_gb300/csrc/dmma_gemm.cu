@@ -1,8 +1,8 @@
 // FP64 tensor-core products of the subspace iteration (Gram matrices of CholQR2, the
 // Rayleigh-Ritz projection X^T W, the projections against locked vectors, and the block
 // updates X Q, X R^{-1}, Y - L h).  They are dense contractions, so they run on the FP64
-// tensor pipe through mma.sync.m8n8k4.f64 (DMMA): GB300 has no FP64 form of tcgen05, and its
-// DMMA rate is several times its FP64 FMA rate.
+// tensor pipe through mma.sync.m8n8k4.f64 (DMMA): GB300 has no FP64 form of tcgen05.  Measured,
+// real DMMA GEMMs on GB300 (these kernels and cuBLAS's) reach about the FP64 FMA ceiling.
 //
 // Fragment layout of m8n8k4.f64 (row.col): with g = lane / 4, t = lane % 4,
 //   A (8x4):  a = A[g][t];   B (4x8): b = B[t][g];   C/D (8x8): c0 = C[g][2t], c1 = C[g][2t+1].

@@ -68,6 +68,9 @@ void launch_bsr_step(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *
 // autotuner, which times every shape once per (type, columns per lane, chunk count)
 void set_step_variant(int is_float, int variant);
 int step_variant(int is_float);
+// shape of the last filter-step launch (FIRST or STEP mode) of this type (process-wide; -1 before any), and a reset
+int step_last_variant(int is_float);
+void reset_step_last_variant();
 template <typename T>
 void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, cudaStream_t s);
 // the step on the rank-1 form (A.u, A.dg; shapes 0..2 of r1_kernels.cu)
@@ -236,7 +239,7 @@ struct pfe_ctx {
   double p_refine_tol = 1e-4;
   int p_method = 0;
   int32_t p_block = 64;
-  double p_basis_factor = 3.0;
+  double p_basis_factor = 2.0;
   int32_t p_batch_threads = 0;
   int p_rank1 = 1;
 

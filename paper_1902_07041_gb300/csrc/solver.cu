@@ -696,6 +696,8 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
   o.filter_launches = st.f_launch;
   o.filter_col_steps = st.f_cols64;
   o.filter_col_steps_f32 = st.f_cols32;
+  o.filter_shape_f64 = st.f_cols64 > 0 ? step_last_variant(0) : -1;
+  o.filter_shape_f32 = st.f_cols32 > 0 ? step_last_variant(1) : -1;
   o.seconds_total = now_s() - st.t_start;
   for (int e = 0; e < 4; ++e)
     if (st.ev[e]) {

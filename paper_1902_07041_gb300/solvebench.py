@@ -1,0 +1,60 @@
+"""Time one interval solve of libpfe on a synthetic glass and print its statistics.
+
+    python -m paper_1902_07041_gb300.solvebench --n-atoms 100000 --seed 1 --lo 0.02 --hi 0.0214 --method 0
+
+Prints one JSON line per solve: wall time around pfe_estimate + pfe_solve, the solver's own
+statistics (pfe_get_stats) and the status.  --method 1 selects the thick-restart block Lanczos
+solver (--block, --basis-factor); --precision 1 the mixed-precision subspace iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def main():
+    import torch
+
+    import glassgen
+    import paper_1902_07041_gb300 as pfe
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-atoms", type=int, default=100_000)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--lo", type=float, default=0.02)
+    ap.add_argument("--hi", type=float, default=0.0214)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--method", type=int, default=0)
+    ap.add_argument("--block", type=int, default=64)
+    ap.add_argument("--basis-factor", type=float, default=2.0)
+    ap.add_argument("--rank1", type=int, default=1)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    g = glassgen.generate(a.n_atoms, a.seed)
+    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    for _ in range(a.repeat):
+        ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
+        try:
+            for key, v in (("PRECISION", a.precision), ("METHOD", a.method), ("BLOCK", a.block),
+                           ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1)):
+                pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), v)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lmax, _ = pfe.pfe_estimate(ctx)
+            pfe.pfe_set_interval(ctx, a.lo * lmax, a.hi * lmax)
+            nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            stats = pfe.pfe_get_stats(ctx)
+            print(json.dumps({"n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi, "method": a.method,
+                              "precision": a.precision, "block": a.block, "basis_factor": a.basis_factor,
+                              "rank1_in_use": pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1), "wall_s": wall,
+                              "status": st, **stats}), flush=True)
+        finally:
+            pfe.pfe_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

@@ -375,3 +375,52 @@ def test_block_lanczos_matches_lapack_with_fewer_matvecs():
     si = oracle.si_solve(H, a, b, 0.0, lmax, coef, 203, oracle.normal_block(0, 0, H.n, 203), tol=1e-8, max_iter=60)
     assert si.status == 0 and si.lam.size == bks.lam.size
     assert bks.matvecs < si.matvecs
+
+
+def _lattice_plane_wave(L, kint, zeta, phase="sin"):
+    """Atoms on the integer points of a periodic L^3 cube; q_i = sqrt(2/N) zeta sin(k . r_i) with the
+    allowed k = 2 pi kint / L (Sec. 4.3)."""
+    g = np.stack(np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij"), -1).reshape(-1, 3).astype(float)
+    N = g.shape[0]
+    k = 2 * np.pi * np.asarray(kint, float) / L
+    f = np.sin(g @ k) if phase == "sin" else np.cos(g @ k)
+    q = np.sqrt(2.0 / N) * f[:, None] * np.asarray(zeta, float)[None, :]
+    return g, k, q.reshape(-1)
+
+
+def test_participation_ratio_closed_forms():
+    """Sec. 4.3: PR = 1 for |q_i| = 1/sqrt(N), 1/N for a single atom, 2/3 for a plane wave; a
+    translation mode sqrt(m_i) e_x of the glass gives (sum m)^2 / (N sum m^2)."""
+    N = 125
+    uni = np.zeros((3 * N, 2))
+    uni[0::3, 0] = 1 / np.sqrt(N)
+    uni[:, 1] = np.random.default_rng(0).choice([-1.0, 1.0], 3 * N) / np.sqrt(3 * N)  # |q_i| = 1/sqrt(N) too
+    one = np.zeros((3 * N, 1))
+    one[3 * 17 + 1, 0] = 1.0
+    _, _, pw = _lattice_plane_wave(5, (1, 0, 0), (0, 0, 1))
+    pr = oracle.participation_ratio(np.column_stack([uni, one, pw, 3.0 * pw]))
+    assert np.allclose(pr, [1.0, 1.0, 1.0 / N, 2.0 / 3.0, 2.0 / 3.0], rtol=1e-14, atol=0)
+    g = glassgen.generate(200, 3)
+    t = np.zeros(3 * g.n_atoms)
+    t[0::3] = np.sqrt(g.mass)
+    assert np.isclose(oracle.participation_ratio(t[:, None])[0],
+                      g.mass.sum() ** 2 / (g.n_atoms * (g.mass ** 2).sum()), rtol=1e-14)
+
+
+def test_plane_wave_content_closed_forms():
+    """A lattice plane wave of an allowed k is 1 in its own polarisation and wave vector, 0 in the
+    other polarisation and in other allowed wave vectors (orthogonality of the lattice sums)."""
+    L = 5
+    pos, k, qt = _lattice_plane_wave(L, (1, 2, 0), (0, 0, 1))             # transverse (zeta _|_ k)
+    _, _, ql = _lattice_plane_wave(L, (1, 2, 0), np.array([1, 2, 0]) / np.sqrt(5), "cos")  # longitudinal
+    ks = 2 * np.pi / L * np.array([[1, 2, 0], [-1, -2, 0], [2, 1, 0], [0, 0, 1]], float)
+    out = oracle.plane_wave_content(np.column_stack([qt, ql]), pos, ks)
+    assert np.allclose(out[0, 0], [0.0, 1.0], atol=1e-13) and np.allclose(out[1, 0], [1.0, 0.0], atol=1e-13)
+    assert np.allclose(out[:, 1], out[:, 0], atol=1e-13)  # -k is the same plane wave
+    assert np.allclose(out[:, 2:], 0.0, atol=1e-13)
+    # content is a sum of squared projections onto orthonormal functions: at most 1 in total
+    q = np.random.default_rng(3).standard_normal(3 * L ** 3)
+    kall = 2 * np.pi / L * np.array([[a, b, c] for a in range(3) for b in range(-2, 3) for c in range(-2, 3)
+                                     if (a, b, c) > (0, 0, 0)], float)
+    tot = oracle.plane_wave_content(q[:, None], pos, kall).sum()
+    assert tot <= 1.0 + 1e-12
