@@ -95,11 +95,19 @@ enum {
   PFE_P_BATCH_THREADS = 24, /* pfe_solve_batch, read from the first context: host threads that run the
                                samples' set-up and dense steps concurrently, each sample on its own
                                stream (0 = automatic: min(samples, hardware threads, 16); 1 = serial) */
-  PFE_P_RANK1 = 25          /* 1 (default): when every off-diagonal block of H is -k r r^T / sqrt(m_i m_j)
+  PFE_P_RANK1 = 25,         /* 1 (default): when every off-diagonal block of H is -k r r^T / sqrt(m_i m_j)
                                (a central-force network, eqs. (1)-(2)) the filter steps use that rank-1
                                form, 6 FMAs a block and column instead of 9; 0: always the full 3x3
                                blocks.  pfe_get_param returns whether the form is in use (it is checked
                                when the filter operator is first built) */
+  PFE_P_FILTER = 26,        /* 0 (default): the piecewise quadratic filter of eq. (fct_f) (both methods);
+                               1: the Dirac filter of eq. (cheby-delta.1), METHOD 1 only (Sec. 2.5: the
+                               paper's production choice with BKS) */
+  PFE_P_PHI = 27,           /* Dirac filter degree: the smallest k whose filter, centred so that
+                               rho(xi) = rho(eta), has rho(xi) / rho(gamma) <= PHI (default 0.8; the phi
+                               of Tables 1-3) */
+  PFE_P_DIRAC_CUT = 28      /* Dirac filter with METHOD 1: Ritz values of rho(Ht) >= DIRAC_CUT x rho(xi) are
+                               wanted (default 0.9) */
 };
 
 /* ---------------------------------------------------------------------------------------
@@ -144,7 +152,8 @@ pfe_status pfe_set_interval(pfe_ctx *ctx, double a, double b);
  * Either output pointer may be NULL.  Needs an interval for the count (else count = NaN). */
 pfe_status pfe_estimate(pfe_ctx *ctx, double *lambda_max, double *count_est);
 
-/* The filter the solver uses (Alg. 3; eqs. (fct_f), (thresh), App. A): degree in *m
+/* The filter the solver uses (Alg. 3; eqs. (fct_f), (thresh), App. A; with PFE_P_FILTER = 1 the
+ * Dirac filter of eq. (cheby-delta.1)): degree in *m
  * and the damped Chebyshev coefficients g_j gamma_j, j = 0..m, in coeffs[0..m] (host; may be
  * NULL to query m only, cap = its length); c and d of eq. (transf.1).  Runs pfe_estimate's
  * lambda_max step first if needed.  PFE_E_CAPACITY if cap < m + 1 (m still stored). */

@@ -61,6 +61,9 @@ def _load():
         _sig(lib, "or_spmm", None, [_P, _I32, _P, _I64, _P, _I64])
         _sig(lib, "or_residuals", None, [_P, _I32, _P, _P, _I64, _P])
         _sig(lib, "or_participation_ratio", None, [_I64, _I32, _P, _I64, _P])
+        _sig(lib, "or_dirac_coeffs", None, [_D, _I32, ctypes.c_int, _P])
+        _sig(lib, "or_dirac_gamma", _D, [_D, _D, _I32, ctypes.c_int])
+        _sig(lib, "or_dirac_degree", _I32, [_D, _D, _D, ctypes.c_int, _I32])
         _sig(lib, "or_plane_wave_content", None, [_I64, _I32, _P, _I64, _P, _I32, _P, _P])
         _sig(lib, "or_pq_coeffs", None, [_D, _D, _D, _I32, _P])
         _sig(lib, "or_chi_coeffs", None, [_D, _D, _I32, _P])
@@ -394,3 +397,20 @@ def plane_wave_content(V, pos, kvecs) -> np.ndarray:
     _load().or_plane_wave_content(V.shape[0] // 3, V.shape[1], _ptr(V), V.shape[0], _ptr(pos), kv.shape[0], _ptr(kv),
                                   _ptr(out))
     return out
+
+
+def dirac_coeffs(gamma, k, kind="jackson") -> np.ndarray:
+    """Damped coefficients of the Dirac filter rho_k(x) centred at gamma (eq. (cheby-delta.1))."""
+    c = np.zeros(k + 1)
+    _load().or_dirac_coeffs(float(gamma), int(k), DAMPING[kind], _ptr(c))
+    return c
+
+
+def dirac_gamma(xi, eta, k, kind="jackson") -> float:
+    """Centre gamma in (xi, eta) with rho_k(xi) = rho_k(eta)."""
+    return _load().or_dirac_gamma(float(xi), float(eta), int(k), DAMPING[kind])
+
+
+def dirac_degree(xi, eta, phi, kind="jackson", kmax=20000) -> int:
+    """Smallest degree whose balanced Dirac filter has rho(xi) / rho(gamma) <= phi."""
+    return _load().or_dirac_degree(float(xi), float(eta), float(phi), DAMPING[kind], int(kmax))

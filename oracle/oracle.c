@@ -1310,3 +1310,52 @@ void or_plane_wave_content(int64_t n_atoms, int32_t k, const double *V, int64_t 
     }
   }
 }
+
+/* ======================================================================================
+ * The Dirac polynomial filter, Sec. 2.5, eq. (cheby-delta.1)
+ * ==================================================================================== */
+
+/* Damped Chebyshev coefficients of the degree-k representative of delta(t - gamma):
+ * c_j = g_j T_j(gamma) / <T_j, T_j>, <T_0, T_0> = pi, <T_j, T_j> = pi / 2 (eq. (cheby-delta.1)),
+ * with the damping factors g_j of or_damping. */
+void or_dirac_coeffs(double gamma, int32_t k, int kind, double *c) {
+  double *g = (double *)malloc(sizeof(double) * (size_t)(k + 1));
+  or_damping(kind, k, g);
+  double th = acos(gamma);
+  for (int32_t j = 0; j <= k; ++j) c[j] = g[j] * cos((double)j * th) / (j == 0 ? OR_PI : OR_PI / 2.0);
+  free(g);
+}
+
+/* gamma in (xi, eta) with rho_k(xi) = rho_k(eta) (Sec. 2.5 and Sec. 3: gamma close to the midpoint),
+ * by bisection on rho_k(xi) - rho_k(eta), which is positive while gamma sits too close to xi. */
+double or_dirac_gamma(double xi, double eta, int32_t k, int kind) {
+  double *c = (double *)malloc(sizeof(double) * (size_t)(k + 1));
+  double lo = xi, hi = eta;
+  for (int it = 0; it < 100; ++it) {
+    double mid = 0.5 * (lo + hi);
+    or_dirac_coeffs(mid, k, kind, c);
+    double f = or_series_value(c, k, xi) - or_series_value(c, k, eta);
+    if (f > 0.0) lo = mid;
+    else hi = mid;
+  }
+  free(c);
+  return 0.5 * (lo + hi);
+}
+
+/* Degree of the Dirac filter: the smallest k >= 2 whose balanced filter has
+ * rho_k(xi) / rho_k(gamma) <= phi (the parameter phi of Tables 1-3: the filter value at the interval
+ * edges relative to its peak).  Returns -1 if no k <= kmax qualifies. */
+int32_t or_dirac_degree(double xi, double eta, double phi, int kind, int32_t kmax) {
+  double *c = (double *)malloc(sizeof(double) * (size_t)(kmax + 1));
+  int32_t found = -1;
+  for (int32_t k = 2; k <= kmax; ++k) {
+    double gm = or_dirac_gamma(xi, eta, k, kind);
+    or_dirac_coeffs(gm, k, kind, c);
+    if (or_series_value(c, k, xi) / or_series_value(c, k, gm) <= phi) {
+      found = k;
+      break;
+    }
+  }
+  free(c);
+  return found;
+}

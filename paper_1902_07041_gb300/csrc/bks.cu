@@ -19,8 +19,10 @@
 //   stop:    every Ritz pair with theta >= theta_cut has residual <= tol_op max|theta|, at least one
 //            block of Ritz values lies below theta_cut, and the number of wanted pairs did not
 //            change since the previous restart.
-// theta_cut = sqrt(r) min(p(xi), p(eta)): below the filter's value at the interval edges and above
-// its value r min(p(xi), p(eta)) outside the margins (eq. (thresh)).
+// theta_cut, piecewise quadratic filter: sqrt(r) min(p(xi), p(eta)), below the filter's value at the
+// interval edges and above its value r min(p(xi), p(eta)) outside the margins (eq. (thresh)).  Dirac
+// filter (eq. (cheby-delta.1), centred so that rho(xi) = rho(eta) = tau, above tau inside the
+// interval): DIRAC_CUT tau, 0.9 tau by default.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -98,8 +100,10 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   const int32_t keep_min = std::min(nev, maxbasis - 2 * bs);
   const int64_t ldv = (maxbasis + bs + 3) / 4 * 4, ldb = (bs + 3) / 4 * 4, ldT = maxbasis;
   cudaStream_t s = ctx->stream;
+  // wanted Ritz values of Op: piecewise quadratic filter, theta >= sqrt(r) min(p(xi), p(eta)); Dirac
+  // filter, theta >= DIRAC_CUT x tau with tau = rho(xi) = rho(eta)
   const double pe = std::min(chebyshev_value(ctx->coef, ctx->m, ctx->xi), chebyshev_value(ctx->coef, ctx->m, ctx->eta));
-  const double theta_cut = std::sqrt(ctx->p_rate) * pe;
+  const double theta_cut = (ctx->p_filter == 1) ? ctx->p_dirac_cut * ctx->dirac_tau : std::sqrt(ctx->p_rate) * pe;
   // n x ldv buffers: V (basis), Vn (next basis, or the wanted Ritz vectors), HW (products with H),
   // Z = ctx->L (the returned eigenvectors)
   BKS_RESERVE(double, V, ctx->w_bks[0], (size_t)n * ldv);

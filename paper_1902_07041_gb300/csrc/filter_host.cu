@@ -115,6 +115,90 @@ int32_t choose_degree(double xi, double eta, double eps, double r, int kind, int
   return -1;
 }
 
+// ---- the Dirac filter of eq. (cheby-delta.1): rho(x) = sum_j g_j T_j(gamma) T_j(x) / <T_j, T_j>
+void dirac_coefficients(double gamma, int32_t m, int kind, std::vector<double> &c) {
+  damping_factors(kind, m, c);
+  // T_j(gamma) by the three-term recurrence
+  double t0 = 1.0, t1 = gamma;
+  for (int32_t j = 0; j <= m; ++j) {
+    double tj;
+    if (j == 0) tj = 1.0;
+    else if (j == 1) tj = gamma;
+    else {
+      tj = 2.0 * gamma * t1 - t0;
+      t0 = t1;
+      t1 = tj;
+    }
+    c[j] *= tj * ((j == 0) ? 1.0 / kPi : 2.0 / kPi);
+  }
+}
+
+// The centre gamma in (xi, eta) with rho(xi) = rho(eta).  rho_gamma(xi) - rho_gamma(eta) is the
+// Chebyshev series sum_j d_j T_j(gamma) with d_j = g_j w_j (T_j(xi) - T_j(eta)); it is positive
+// while gamma lies too close to xi.  Its sign change in (xi, eta) is found by bisection.
+double dirac_center(double xi, double eta, int32_t m, int kind) {
+  std::vector<double> d;
+  damping_factors(kind, m, d);
+  double a0 = 1.0, a1 = xi, b0 = 1.0, b1 = eta;
+  for (int32_t j = 0; j <= m; ++j) {
+    double ta, tb;
+    if (j == 0) {
+      ta = tb = 1.0;
+    } else if (j == 1) {
+      ta = xi;
+      tb = eta;
+    } else {
+      ta = 2.0 * xi * a1 - a0;
+      a0 = a1;
+      a1 = ta;
+      tb = 2.0 * eta * b1 - b0;
+      b0 = b1;
+      b1 = tb;
+    }
+    d[j] *= (ta - tb) * ((j == 0) ? 1.0 / kPi : 2.0 / kPi);
+  }
+  double lo = xi, hi = eta;
+  for (int it = 0; it < 80 && hi - lo > 1e-17; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (chebyshev_value(d, m, mid) > 0.0) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+namespace {
+// rho(xi) / rho(gamma) of the balanced degree-m filter
+double dirac_edge_ratio(double xi, double eta, int32_t m, int kind) {
+  const double g = dirac_center(xi, eta, m, kind);
+  std::vector<double> c((size_t)m + 1);
+  dirac_coefficients(g, m, kind, c);
+  return chebyshev_value(c, m, xi) / chebyshev_value(c, m, g);
+}
+}  // namespace
+
+int32_t choose_dirac_degree(double xi, double eta, double phi, int kind, int32_t kmax) {
+  // the edge ratio falls with the degree: bracket by doubling, bisect, then step down while the
+  // next lower degree still qualifies
+  int32_t hi = 2;
+  while (hi <= kmax && dirac_edge_ratio(xi, eta, hi, kind) > phi) hi *= 2;
+  if (hi > kmax) {
+    hi = kmax;
+    if (dirac_edge_ratio(xi, eta, hi, kind) > phi) return -1;
+  }
+  int32_t lo = std::max(2, hi / 2);  // lo fails (or is the start), hi qualifies
+  if (lo == hi || dirac_edge_ratio(xi, eta, lo, kind) <= phi) {
+    hi = lo;
+  } else {
+    while (hi - lo > 1) {
+      const int32_t mid = (lo + hi) / 2;
+      if (dirac_edge_ratio(xi, eta, mid, kind) <= phi) hi = mid;
+      else lo = mid;
+    }
+  }
+  while (hi > 2 && dirac_edge_ratio(xi, eta, hi - 1, kind) <= phi) --hi;
+  return hi;
+}
+
 void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &beta, double *theta, double *last) {
   const int n = (int)alpha.size();
   // Gershgorin bounds

@@ -175,6 +175,11 @@ void damping_factors(int kind, int32_t m, std::vector<double> &g);
 double chebyshev_value(const std::vector<double> &c, int32_t m, double x);
 // smallest degree satisfying eq. (thresh), or -1
 int32_t choose_degree(double xi, double eta, double eps, double r, int kind, int32_t kmax);
+// Dirac filter of eq. (cheby-delta.1): damped coefficients for centre gamma; the centre with equal
+// values at xi and eta; the smallest degree whose balanced filter has rho(xi) / rho(gamma) <= phi
+void dirac_coefficients(double gamma, int32_t m, int kind, std::vector<double> &c);
+double dirac_center(double xi, double eta, int32_t m, int kind);
+int32_t choose_dirac_degree(double xi, double eta, double phi, int kind, int32_t kmax);
 // largest eigenvalue of a symmetric tridiagonal matrix and the last entry of its unit eigenvector
 void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &beta, double *theta, double *last);
 
@@ -242,6 +247,8 @@ struct pfe_ctx {
   double p_basis_factor = 2.0;
   int32_t p_batch_threads = 0;
   int p_rank1 = 1;
+  int p_filter = 0;
+  double p_phi = 0.8, p_dirac_cut = 0.9;
 
   // state
   bool has_interval = false;
@@ -254,6 +261,7 @@ struct pfe_ctx {
   int32_t m = 0;
   std::vector<double> coef;
   double tc = 0, td = 0, xi = 0, eta = 0, eps = 0;
+  double dirac_gamma = 0, dirac_tau = 0;  // Dirac filter: centre and the (equal) value at xi and eta
 
   // results
   bool has_result = false;

@@ -245,6 +245,18 @@ pfe_status ensure_filter(pfe_ctx *ctx) {
   ctx->eta = (ctx->b - ctx->tc) / ctx->td;
   ctx->eps = ctx->p_eps_frac * (ctx->eta - ctx->xi);
   int32_t m = ctx->p_degree;
+  if (ctx->p_filter == 1) {  // the Dirac filter of eq. (cheby-delta.1), centred so that rho(xi) = rho(eta)
+    if (m <= 0) {
+      m = choose_dirac_degree(ctx->xi, ctx->eta, ctx->p_phi, ctx->p_damping, 60000);
+      if (m < 0) return pfe_fail(ctx, PFE_E_ARG, "no Dirac filter degree <= 60000 meets PHI");
+    }
+    ctx->dirac_gamma = dirac_center(ctx->xi, ctx->eta, m, ctx->p_damping);
+    dirac_coefficients(ctx->dirac_gamma, m, ctx->p_damping, ctx->coef);
+    ctx->dirac_tau = std::min(chebyshev_value(ctx->coef, m, ctx->xi), chebyshev_value(ctx->coef, m, ctx->eta));
+    ctx->m = m;
+    ctx->has_filter = true;
+    return PFE_OK;
+  }
   if (m <= 0) {
     m = choose_degree(ctx->xi, ctx->eta, ctx->eps, ctx->p_rate, ctx->p_damping, 60000);
     if (m < 0) return pfe_fail(ctx, PFE_E_ARG, "no filter degree <= 60000 meets the rate; widen eps or r");
@@ -417,6 +429,9 @@ pfe_status project_out(pfe_ctx *ctx, const double *L, int32_t nl, double *Y, int
 // solve_filter by one batched persistent launch per Chebyshev step.
 pfe_status solve_setup(pfe_ctx *ctx) {
   SolveState &st = ctx->solve;
+  if (ctx->p_filter != 0)
+    return pfe_fail(ctx, PFE_E_ARG, "the subspace iteration uses the piecewise quadratic filter (FILTER 0); "
+                                    "the Dirac filter is for the block Lanczos method (METHOD 1)");
   for (int e = 0; e < 4; ++e)
     if (st.ev[e]) cudaEventDestroy(st.ev[e]);
   for (int e = 0; e < 2; ++e)
@@ -1230,6 +1245,20 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!int_ok(0) || v > 256) return pfe_fail(ctx, PFE_E_ARG, "BATCH_THREADS must be an integer in [0, 256]");
       ctx->p_batch_threads = (int32_t)v;
       break;
+    case PFE_P_FILTER:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "FILTER must be 0 or 1");
+      ctx->p_filter = (int)v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_PHI:
+      if (!(v > 0 && v < 1)) return pfe_fail(ctx, PFE_E_ARG, "PHI must be in (0, 1)");
+      ctx->p_phi = v;
+      ctx->has_filter = false;
+      break;
+    case PFE_P_DIRAC_CUT:
+      if (!(v > 0 && v <= 1)) return pfe_fail(ctx, PFE_E_ARG, "DIRAC_CUT must be in (0, 1]");
+      ctx->p_dirac_cut = v;
+      break;
     case PFE_P_RANK1:
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "RANK1 must be 0 or 1");
       ctx->p_rank1 = (int)v;
@@ -1273,6 +1302,9 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_BASIS_FACTOR: *v = ctx->p_basis_factor; break;
     case PFE_P_BATCH_THREADS: *v = ctx->p_batch_threads; break;
     case PFE_P_RANK1: *v = (ctx->p_rank1 && ctx->r1_state == 1) ? 1.0 : 0.0; break;
+    case PFE_P_FILTER: *v = ctx->p_filter; break;
+    case PFE_P_PHI: *v = ctx->p_phi; break;
+    case PFE_P_DIRAC_CUT: *v = ctx->p_dirac_cut; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;

@@ -123,3 +123,59 @@ def test_paper_diagonal_test_case_1():
     assert np.allclose(lam, lam_all[sel], rtol=0, atol=1e-12)
     idx = np.nonzero(sel)[0]
     assert np.allclose(np.abs(V[idx, np.arange(50)]), 1.0, atol=1e-8)
+
+
+@pytest.mark.parametrize("table,xi,eta", [(1, -0.9, -0.898), (2, -0.9, -0.896), (3, -0.9, -0.885)])
+def test_library_dirac_degrees_match_tables(golden, table, xi, eta):
+    """The library's own Dirac-filter degree selection reproduces the degrees printed in Tables 1-3
+    (transformed interval [xi, eta] with lambda in [0, 2]: a = 1 + xi, b = 1 + eta)."""
+    fx = golden("dirac_degrees_tables_1_3.json")
+    case = [c for c in fx["cases"] if c["table"] == table][0]
+    rp, ci, vals = _block_diagonal(np.linspace(0.0, 2.0, 300))
+    ctx = pfe.pfe_create(100, rp, ci, vals, None)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_LAMBDA_MAX, 2.0)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_FILTER, 1)
+        for i, phi in enumerate(fx["rows_phi"]):
+            for j, kind in enumerate(fx["columns"]):
+                pfe.pfe_set_param(ctx, pfe.PFE_P_PHI, phi)
+                pfe.pfe_set_param(ctx, pfe.PFE_P_DAMPING, {"none": 0, "jackson": 1, "lanczos": 2}[kind])
+                pfe.pfe_set_interval(ctx, 1.0 + xi, 1.0 + eta)
+                m, coef, c, d = pfe.pfe_get_filter(ctx)
+                assert m == case["degrees"][i][j], (table, phi, kind, m)
+                g = oracle.dirac_gamma(xi, eta, m, kind)
+                assert np.allclose(coef, oracle.dirac_coeffs(g, m, kind), rtol=1e-9, atol=1e-12 * np.abs(coef).max())
+    finally:
+        pfe.pfe_destroy(ctx)
+
+
+def test_block_lanczos_dirac_filter_paper_test_case_1():
+    """Sec. 4.1 test case 1 with the paper's production solver: block Lanczos on the Dirac filter
+    (phi = 0.8, Jackson smoothing), the 50 eigenvalues of [0.1, 0.102] and their coordinate vectors."""
+    lam_all = -1 + (2 * np.arange(1, 50001) - 1) / 50000.0 + 1.0
+    lam_all = np.append(lam_all, 2.0)
+    rp, ci, vals = _block_diagonal(lam_all)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, 50001 // 3, None, 0.1, 0.102, absolute=True, LAMBDA_MAX=2.0,
+                                        METHOD=1, FILTER=1, DAMPING=1, BLOCK=16)
+    sel = (lam_all >= a) & (lam_all <= b)
+    assert st == pfe.PFE_OK and nf == 50
+    assert np.allclose(lam, lam_all[sel], rtol=0, atol=1e-12)
+    idx = np.nonzero(sel)[0]
+    assert np.allclose(np.abs(V[idx, np.arange(50)]), 1.0, atol=1e-8)
+
+
+def test_block_lanczos_dirac_filter_glass():
+    g, (rp, ci, vals) = _glass(300, 5)
+    st, nf, lam, V, lmax, a, b = _solve(rp, ci, vals, g.n_atoms, g.mass, 0.05, 0.12, METHOD=1, FILTER=1, DAMPING=1,
+                                        BLOCK=32)
+    H = oracle.csr_from_springs(g)
+    w, _, _ = oracle.exact_interval(H, a, b)
+    assert st == pfe.PFE_OK and nf == w.size
+    assert np.allclose(lam, w, rtol=1e-10, atol=0)
+    assert np.all(oracle.residuals(H, lam, V) <= 1e-8 * lmax)
+
+
+def test_subspace_iteration_refuses_the_dirac_filter():
+    g, (rp, ci, vals) = _glass(100, 5)
+    st, nf, *_ = _solve(rp, ci, vals, g.n_atoms, g.mass, 0.05, 0.12, FILTER=1)
+    assert st == pfe.PFE_E_ARG and nf == 0

@@ -22,7 +22,9 @@ def _device():
 
 def test_single_atom_modes_of_a_diagonal_matrix():
     """Diagonal H with distinct entries: every eigenvector is a coordinate vector e_{3i+d}, so
-    PR = 1/N and the plane-wave content is (2/N) (khat_d^2, 1 - khat_d^2)."""
+    PR = 1/N and the plane-wave content is (2/N) (khat_d^2, 1 - khat_d^2).  Solved by block Lanczos,
+    whose residuals sit near rounding: the content is linear in the eigenvector error (the
+    participation ratio of a coordinate vector only quadratic)."""
     N = 300
     d = np.linspace(0.01, 1.0, 3 * N)
     rp = np.arange(N + 1, dtype=np.int32)
@@ -33,6 +35,8 @@ def test_single_atom_modes_of_a_diagonal_matrix():
     ctx = pfe.pfe_create(N, rp, ci, vals, None)
     try:
         pfe.pfe_set_param(ctx, pfe.PFE_P_LAMBDA_MAX, 1.01)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, 1)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_BLOCK, 16)
         pfe.pfe_set_interval(ctx, 0.30, 0.34)
         nf, _ = pfe.pfe_solve(ctx)
         sel = np.nonzero((d >= 0.30) & (d <= 0.34))[0]
@@ -45,7 +49,7 @@ def test_single_atom_modes_of_a_diagonal_matrix():
         E = np.zeros((3 * N, nf))
         E[sel, np.arange(nf)] = 1.0
         ref = oracle.plane_wave_content(E, pos, ks)
-        assert np.allclose(out, ref, rtol=1e-12, atol=1e-15)
+        assert np.allclose(out, ref, rtol=1e-9, atol=1e-13)
     finally:
         pfe.pfe_destroy(ctx)
 

@@ -424,3 +424,32 @@ def test_plane_wave_content_closed_forms():
                                      if (a, b, c) > (0, 0, 0)], float)
     tot = oracle.plane_wave_content(q[:, None], pos, kall).sum()
     assert tot <= 1.0 + 1e-12
+
+
+def test_dirac_filter_degrees_tables_1_3(golden):
+    """All 18 Dirac-filter degrees printed in Tables 1-3 (phi = 0.8, 0.6; Jackson, Lanczos, none):
+    the smallest degree whose filter, centred so that rho(xi) = rho(eta), has rho(xi) / rho(gamma) <= phi."""
+    fx = golden("dirac_degrees_tables_1_3.json")
+    for case in fx["cases"]:
+        for i, phi in enumerate(fx["rows_phi"]):
+            for j, kind in enumerate(fx["columns"]):
+                assert oracle.dirac_degree(case["xi"], case["eta"], phi, kind) == case["degrees"][i][j], \
+                    (case["table"], phi, kind)
+
+
+def test_dirac_filter_is_the_delta_projection():
+    """rho_k = sum_j T_j(gamma) T_j / <T_j, T_j>: undamped, its integral against any polynomial f of
+    degree <= k with the Chebyshev weight returns f(gamma) (the defining property of delta); the
+    balanced centre gives equal edge values."""
+    gm, k = -0.37, 12
+    c = oracle.dirac_coeffs(gm, k, "none")
+    x, w = np.polynomial.chebyshev.chebgauss(64)  # exact for degree <= 127 with weight 1/sqrt(1-x^2)
+    for deg in (0, 3, 7, 12):
+        f = np.polynomial.chebyshev.Chebyshev.basis(deg) + 0.5 * np.polynomial.chebyshev.Chebyshev.basis(max(deg - 2, 0))
+        integral = np.sum(w * f(x) * np.polynomial.chebyshev.chebval(x, c))
+        assert abs(integral - f(gm)) <= 1e-12
+    xi, eta = -0.9, -0.885
+    g = oracle.dirac_gamma(xi, eta, 128, "jackson")
+    c = oracle.dirac_coeffs(g, 128, "jackson")
+    assert xi < g < eta
+    assert abs(oracle.series_value(c, xi) - oracle.series_value(c, eta)) <= 1e-12 * oracle.series_value(c, g)
