@@ -106,8 +106,9 @@ enum {
   PFE_P_PHI = 27,           /* Dirac filter degree: the smallest k whose filter, centred so that
                                rho(xi) = rho(eta), has rho(xi) / rho(gamma) <= PHI (default 0.8; the phi
                                of Tables 1-3) */
-  PFE_P_DIRAC_CUT = 28      /* Dirac filter with METHOD 1: Ritz values of rho(Ht) >= DIRAC_CUT x rho(xi) are
+  PFE_P_DIRAC_CUT = 28,     /* Dirac filter with METHOD 1: Ritz values of rho(Ht) >= DIRAC_CUT x rho(xi) are
                                wanted (default 0.9) */
+  PFE_P_SLICE_TARGET = 29   /* pfe_solve_sliced: eigenvalues per slice the automatic edges aim at (default 1000) */
 };
 
 /* ---------------------------------------------------------------------------------------
@@ -205,6 +206,7 @@ typedef struct {
   int32_t filter_shape_f64;    /* kernel shape of the last FP64 filter step (PFE_P_STEP_SHAPE_F64 numbering;
                                   7-9: the rank-1 form), -1 if none ran */
   int32_t filter_shape_f32;    /* the same for the FP32 filter step */
+  int32_t slices;              /* pfe_solve_sliced: number of slices (0 for the other solves) */
 } pfe_stats;
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 
@@ -274,7 +276,24 @@ pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeff
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
 
 /* ---------------------------------------------------------------------------------------
- * Analysis of the computed modes (Sec. 4.3).  A mode q is read as N 3-vectors q_i, the three
+ * Spectrum slicing (Sec. 2.6 and Sec. 5: split [a, b] into sub-intervals of a reasonable
+ * eigenvalue count, e.g. for memory; Sec. 4.3 computes one interval as five)
+ * ------------------------------------------------------------------------------------- */
+
+/* All eigenpairs in the context's interval [a, b], computed slice by slice with the selected method
+ * and merged; results and statistics as for pfe_solve (the statistics summed over the slices).
+ * nedges = 0 (edges NULL): automatic edges, about PFE_P_SLICE_TARGET eigenvalues per slice, placed by
+ * the cumulative count of the stochastic density of states (Sec. 2.4's estimator with Chebyshev
+ * moments of degree D, so every slice count comes from one set of moments); one slice means pfe_solve.
+ * Otherwise edges[0..nedges-1] (host) are the interior edges, strictly increasing inside (a, b).
+ * Each slice is solved on its interval widened by 1e-6 lambda_max at its interior edges; the pairs
+ * that two neighbouring slices return within 2e-6 lambda_max of their shared edge are merged by a
+ * Rayleigh-Ritz step with H on their joint span (a pair found twice counts once).  Device memory:
+ * the eigenvectors of all slices (n x found, FP64) beside one slice's solver buffers. */
+pfe_status pfe_solve_sliced(pfe_ctx *ctx, int32_t nedges, const double *edges, int32_t *n_found);
+
+/* ---------------------------------------------------------------------------------------
+ * Analysis of the computed modes (Sec. 4.4).  A mode q is read as N 3-vectors q_i, the three
  * dof rows of atom i; both calls work on the context's found eigenvectors, on the device, in the
  * order of pfe_get_eigenpairs.  PFE_E_STATE without solve results; PFE_E_CAPACITY if cap < n_found.
  * ------------------------------------------------------------------------------------- */
@@ -286,7 +305,7 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
 pfe_status pfe_participation_ratio(pfe_ctx *ctx, int32_t cap, double *pr);
 
 /* Plane-wave content of each mode for nk wave vectors (the identification of sound modes by
- * wave vector k = 2 pi (m, n, l) / L and polarisation in Sec. 4.3).  With
+ * wave vector k = 2 pi (m, n, l) / L and polarisation in Sec. 4.4).  With
  * A_d = sum_i q_{i,d} exp(i k . r_i) (d = x, y, z), k^ = k / |k|:
  *     out[2 (s nk + w)]     = (2/N) |k^ . A|^2 / |q|^2            (longitudinal)
  *     out[2 (s nk + w) + 1] = (2/N) (|A|^2 - |k^ . A|^2) / |q|^2  (transverse, both polarisations)

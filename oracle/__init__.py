@@ -381,7 +381,7 @@ def exact_interval(H: CSR, a, b):
 
 
 def participation_ratio(V) -> np.ndarray:
-    """Normalised participation ratio of each column (Sec. 4.3, eq. (PR_def) divided by N)."""
+    """Normalised participation ratio of each column (Sec. 4.4, eq. (PR_def) divided by N)."""
     V = _fortran(np.asarray(V, np.float64).reshape(np.shape(V)[0], -1))
     pr = np.zeros(V.shape[1])
     _load().or_participation_ratio(V.shape[0] // 3, V.shape[1], _ptr(V), V.shape[0], _ptr(pr))
@@ -389,7 +389,7 @@ def participation_ratio(V) -> np.ndarray:
 
 
 def plane_wave_content(V, pos, kvecs) -> np.ndarray:
-    """(k, nk, 2): longitudinal and transverse plane-wave content of each column (Sec. 4.3)."""
+    """(k, nk, 2): longitudinal and transverse plane-wave content of each column (Sec. 4.4)."""
     V = _fortran(np.asarray(V, np.float64).reshape(np.shape(V)[0], -1))
     pos = _f64(np.asarray(pos).reshape(-1))
     kv = _f64(np.asarray(kvecs).reshape(-1, 3))

@@ -1251,7 +1251,7 @@ int or_bks_solve(const or_csr *H, double a, double b, double lmin, double lmax, 
 }
 
 /* ======================================================================================
- * Analysis of the computed modes, Sec. 4.3
+ * Analysis of the computed modes, Sec. 4.4
  * ==================================================================================== */
 
 /* Participation ratio, eq. (PR_def): PR = 1 / sum_i |q_i|^4 for a mode of unit 2-norm, q_i the
@@ -1272,7 +1272,7 @@ void or_participation_ratio(int64_t n_atoms, int32_t k, const double *V, int64_t
   }
 }
 
-/* Plane-wave content of each mode for wave vectors kvec[w] (Sec. 4.3: a plane wave of wave
+/* Plane-wave content of each mode for wave vectors kvec[w] (Sec. 4.4: a plane wave of wave
  * vector k and polarisation zeta is q_i = sqrt(2/N) zeta sin(k . r_i), r_i the atom position):
  * the squared projections onto sqrt(2/N) zeta sin(k . r_i) and sqrt(2/N) zeta cos(k . r_i), summed
  * over both and over the polarisations along k (out[.. 0]) and across k (out[.. 1]), divided by

@@ -34,14 +34,14 @@ PFE_P_LAMBDA_MAX, PFE_P_LAMBDA_MIN, PFE_P_COUNT_M, PFE_P_COUNT_DEGREE = 11, 12, 
 PFE_P_LANCZOS_STEPS, PFE_P_COUNT_DAMPING, PFE_P_MIN_WIDTH, PFE_P_REFINE_TOL = 15, 16, 17, 18
 PFE_P_STEP_SHAPE_F64, PFE_P_STEP_SHAPE_F32 = 19, 20
 PFE_P_METHOD, PFE_P_BLOCK, PFE_P_BASIS_FACTOR, PFE_P_BATCH_THREADS, PFE_P_RANK1 = 21, 22, 23, 24, 25
-PFE_P_FILTER, PFE_P_PHI, PFE_P_DIRAC_CUT = 26, 27, 28
+PFE_P_FILTER, PFE_P_PHI, PFE_P_DIRAC_CUT, PFE_P_SLICE_TARGET = 26, 27, 28, 29
 
 # every entry point declared in include/pfe.h
 EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", "pfe_set_param",
            "pfe_get_param", "pfe_set_interval", "pfe_estimate", "pfe_get_filter", "pfe_solve",
            "pfe_get_eigenpairs", "pfe_get_stats", "pfe_filter_apply", "pfe_filter_adjoint",
            "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc", "pfe_participation_ratio",
-           "pfe_plane_wave_content")
+           "pfe_plane_wave_content", "pfe_solve_sliced")
 
 
 class PfeError(RuntimeError):
@@ -61,7 +61,7 @@ class PfeStats(ctypes.Structure):
                 ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
                 ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64),
                 ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32), ("filter_shape_f64", ctypes.c_int32),
-                ("filter_shape_f32", ctypes.c_int32)]
+                ("filter_shape_f32", ctypes.c_int32), ("slices", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "pfe_filter_apply_noalloc": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _I64, _P]),
         "pfe_participation_ratio": (ctypes.c_int, [_P, _I32, _P]),
         "pfe_plane_wave_content": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P]),
+        "pfe_solve_sliced": (ctypes.c_int, [_P, _I32, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -312,3 +313,17 @@ def pfe_plane_wave_content(ctx, pos, kvecs, cap):
                                        int(cap), out.ctypes.data)
     _check(st, ctx)
     return out
+
+
+def pfe_solve_sliced(ctx, edges=None, raise_on_error=True):
+    """Spectrum slicing of the context's interval; edges None = automatic (PFE_P_SLICE_TARGET per
+    slice), else the interior edges. Returns (n_found, status)."""
+    nf = ctypes.c_int32(0)
+    if edges is None or len(edges) == 0:
+        st = load().pfe_solve_sliced(ctx, 0, None, ctypes.byref(nf))
+    else:
+        ed = _host(edges, np.float64)
+        st = load().pfe_solve_sliced(ctx, int(ed.size), ed.ctypes.data, ctypes.byref(nf))
+    if raise_on_error and st != PFE_OK:
+        _check(st, ctx)
+    return nf.value, st

@@ -1,4 +1,4 @@
-// Analysis of the computed modes (Sec. 4.3): the participation ratio of eq. (PR_def) and the
+// Analysis of the computed modes (Sec. 4.4): the participation ratio of eq. (PR_def) and the
 // plane-wave content of each eigenvector.  A mode q is read as N 3-vectors q_i (the three dof
 // rows of atom i).
 //

@@ -249,6 +249,7 @@ struct pfe_ctx {
   int p_rank1 = 1;
   int p_filter = 0;
   double p_phi = 0.8, p_dirac_cut = 0.9;
+  int32_t p_slice_target = 1000;
 
   // state
   bool has_interval = false;
@@ -274,7 +275,7 @@ struct pfe_ctx {
 
   // workspaces
   pfe::DBuf w_X, w_Y, w_W, w_T0, w_T1, w_T2, w_small, w_small2, w_red, w_idx, w_cs_work, w_info, w_f32a, w_f32b,
-      w_f32c, w_f32d, w_ckpt, w_rr, w_gram, w_bks[5];
+      w_f32c, w_f32d, w_ckpt, w_rr, w_gram, w_bks[5], w_slice[2];
   int64_t launch_base = 0;  // process-wide launch counter when the context was created
   SolveState solve;
   pfe::DBuf dcoef;            // filter coefficients on the device (batched solves)
@@ -294,6 +295,9 @@ pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64
                           bool *shifted = nullptr);
 pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1);
 double solver_now();
+pfe_status solver_ensure_lmax(pfe_ctx *ctx);
+Bsr<double> solver_bsr_H(const pfe_ctx *ctx);     // H
+Bsr<double> solver_bsr_Hs64(const pfe_ctx *ctx);  // the filter operator A = (2/d)(H - cI)
 }  // namespace pfe
 
 // status helpers used across the host sources

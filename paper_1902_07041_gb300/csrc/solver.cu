@@ -937,6 +937,9 @@ pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X,
   return run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k, ld, X, Y, b0, b1, ctx->stream);
 }
 double solver_now() { return now_s(); }
+pfe_status solver_ensure_lmax(pfe_ctx *ctx) { return ensure_lmax(ctx); }
+Bsr<double> solver_bsr_H(const pfe_ctx *ctx) { return bsr_H(ctx); }
+Bsr<double> solver_bsr_Hs64(const pfe_ctx *ctx) { return bsr_Hs64(ctx); }
 }  // namespace pfe
 
 // =====================================================================================
@@ -1128,7 +1131,7 @@ void pfe_destroy(pfe_ctx *ctx) {
                   &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram,
                   &ctx->w_bks[0], &ctx->w_bks[1], &ctx->w_bks[2], &ctx->w_bks[3], &ctx->w_bks[4],
                   &ctx->r1_rp, &ctx->r1_ci, &ctx->r1_u64, &ctx->r1_dg64, &ctx->r1_u32, &ctx->r1_dg32,
-                  &ctx->r1_flag};
+                  &ctx->r1_flag, &ctx->w_slice[0], &ctx->w_slice[1]};
   for (DBuf *b : bufs) dbuf_free(*b);
   for (int e = 0; e < 4; ++e)
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
@@ -1259,6 +1262,10 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!(v > 0 && v <= 1)) return pfe_fail(ctx, PFE_E_ARG, "DIRAC_CUT must be in (0, 1]");
       ctx->p_dirac_cut = v;
       break;
+    case PFE_P_SLICE_TARGET:
+      if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "SLICE_TARGET must be an integer >= 1");
+      ctx->p_slice_target = (int32_t)v;
+      break;
     case PFE_P_RANK1:
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "RANK1 must be 0 or 1");
       ctx->p_rank1 = (int)v;
@@ -1305,6 +1312,7 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_FILTER: *v = ctx->p_filter; break;
     case PFE_P_PHI: *v = ctx->p_phi; break;
     case PFE_P_DIRAC_CUT: *v = ctx->p_dirac_cut; break;
+    case PFE_P_SLICE_TARGET: *v = ctx->p_slice_target; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;

@@ -179,3 +179,59 @@ def test_subspace_iteration_refuses_the_dirac_filter():
     g, (rp, ci, vals) = _glass(100, 5)
     st, nf, *_ = _solve(rp, ci, vals, g.n_atoms, g.mass, 0.05, 0.12, FILTER=1)
     assert st == pfe.PFE_E_ARG and nf == 0
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_spectrum_slicing_matches_exact(method):
+    """pfe_solve_sliced with automatic, count-guided edges (about 40 eigenvalues a slice): the union is
+    every eigenpair of [a, b] exactly once."""
+    g, (rp, ci, vals) = _glass(1000, 0)
+    ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, method)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_BLOCK, 16)
+        pfe.pfe_set_param(ctx, pfe.PFE_P_SLICE_TARGET, 40)
+        lmax, _ = pfe.pfe_estimate(ctx)
+        a, b = 0.02 * lmax, 0.05 * lmax
+        pfe.pfe_set_interval(ctx, a, b)
+        nf, st = pfe.pfe_solve_sliced(ctx)
+        stats = pfe.pfe_get_stats(ctx)
+        lam, V, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
+    finally:
+        pfe.pfe_destroy(ctx)
+    H = oracle.csr_from_springs(g)
+    w, _, _ = oracle.exact_interval(H, a, b)
+    assert st == pfe.PFE_OK and stats["slices"] >= 3
+    assert nf == w.size and np.allclose(lam, w, rtol=1e-10, atol=0)
+    assert np.all(oracle.residuals(H, lam, V) <= 1e-8 * lmax)
+    # vectors of different slices are orthogonal to the accuracy the residuals allow
+    assert np.max(np.abs(V.T @ V - np.eye(nf))) <= (1e-4 if method == 0 else 1e-9)
+
+
+def test_spectrum_slicing_edges_on_eigenvalues():
+    """Explicit edges placed exactly on a simple and on a double eigenvalue: both neighbouring slices
+    find those pairs, and the merge keeps each eigenpair once (the double one as a 2-dimensional
+    space)."""
+    d = np.linspace(0.01, 1.0, 600)
+    d[300] = d[301] = 0.5  # a double eigenvalue
+    simple = d[250]
+    rp, ci, vals = _block_diagonal(np.concatenate([d, [1.0, 1.0, 1.0]]))
+    N = (d.size + 3) // 3
+    ctx = pfe.pfe_create(N, rp, ci, vals, None)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_LAMBDA_MAX, 1.01)
+        a, b = 0.38, 0.62
+        pfe.pfe_set_interval(ctx, a, b)
+        nf, st = pfe.pfe_solve_sliced(ctx, [simple, 0.5])
+        lam, V, res = pfe.pfe_get_eigenpairs(ctx, 3 * N, nf)
+        stats = pfe.pfe_get_stats(ctx)
+    finally:
+        pfe.pfe_destroy(ctx)
+    full = np.concatenate([d, [1.0, 1.0, 1.0]])
+    sel = np.sort(full[(full >= a) & (full <= b)])
+    assert st == pfe.PFE_OK and stats["slices"] == 3
+    assert nf == sel.size and np.allclose(lam, sel, rtol=0, atol=1e-12)
+    assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-8
+    # the double eigenvalue's two vectors span the coordinates 300 and 301
+    j = np.nonzero(np.abs(lam - 0.5) < 1e-9)[0]
+    assert j.size == 2 and np.allclose(np.linalg.norm(V[[300, 301]][:, j], axis=0), 1.0, atol=1e-8)

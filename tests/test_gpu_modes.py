@@ -1,4 +1,4 @@
-"""Mode analysis of Sec. 4.3 on the GPU (participation ratio, plane-wave content), through the C ABI,
+"""Mode analysis of Sec. 4.4 on the GPU (participation ratio, plane-wave content), through the C ABI,
 against the oracle on eigenvectors that the oracle or the construction fixes."""
 import numpy as np
 import pytest

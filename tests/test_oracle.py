@@ -379,7 +379,7 @@ def test_block_lanczos_matches_lapack_with_fewer_matvecs():
 
 def _lattice_plane_wave(L, kint, zeta, phase="sin"):
     """Atoms on the integer points of a periodic L^3 cube; q_i = sqrt(2/N) zeta sin(k . r_i) with the
-    allowed k = 2 pi kint / L (Sec. 4.3)."""
+    allowed k = 2 pi kint / L (Sec. 4.4)."""
     g = np.stack(np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij"), -1).reshape(-1, 3).astype(float)
     N = g.shape[0]
     k = 2 * np.pi * np.asarray(kint, float) / L
@@ -389,7 +389,7 @@ def _lattice_plane_wave(L, kint, zeta, phase="sin"):
 
 
 def test_participation_ratio_closed_forms():
-    """Sec. 4.3: PR = 1 for |q_i| = 1/sqrt(N), 1/N for a single atom, 2/3 for a plane wave; a
+    """Sec. 4.4: PR = 1 for |q_i| = 1/sqrt(N), 1/N for a single atom, 2/3 for a plane wave; a
     translation mode sqrt(m_i) e_x of the glass gives (sum m)^2 / (N sum m^2)."""
     N = 125
     uni = np.zeros((3 * N, 2))
