@@ -36,14 +36,18 @@ WORKLOADS = {
     "glass-n100k-mixed": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=1),
     "glass-n1k-fp64": dict(N=1_000, seed=0, lo=0.02, hi=0.05, precision=0),
     "glass-n20k-fp64": dict(N=20_000, seed=1, lo=0.02, hi=0.0214, precision=0),
+    # the literal N = 100,000 interval [0.02, 0.03] lambda_max (~4,980 modes): spectrum slicing into
+    # slices of ~700 modes, each solved by block Lanczos
+    "glass-n100k-literal-sliced": dict(N=100_000, seed=1, lo=0.02, hi=0.03, precision=0, method=1, sliced=700),
 }
 DEFAULT = "glass-n100k-fp64"
 
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
-# DRAM traffic / algorithmic bytes of the fused step on full 3x3 blocks, from one ncu capture per
-# type (N = 100,000; k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md,
-# filter_step_f32_n100k.md).  The rank-1 kernel has no capture yet: its traffic is reported null.
-TRAFFIC_RATIO = {("bsr", 8): 872.490752 / 854.171476, ("bsr", 4): 830.966784 / 813.542884}
+# DRAM traffic / algorithmic bytes of the fused step, from one ncu capture per form and type
+# (N = 100,000; k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md, filter_step_f32_n100k.md,
+# filter_step_r1_f64_n100k.md, filter_step_r1_f32_n100k.md)
+TRAFFIC_RATIO = {("bsr", 8): 872.490752 / 854.171476, ("bsr", 4): 830.966784 / 813.542884,
+                 ("rank1", 8): 818.178048 / 802.000020, ("rank1", 4): 800.012800 / 787.257156}
 R1_SHAPES = (7, 8, 9)  # kernel shapes of the fused step that run on the rank-1 form
 
 
@@ -145,11 +149,13 @@ def one_step(pfe, torch, g, rp, ci, vals, wl, ev):
     try:
         pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, wl["precision"])
         pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, wl.get("method", 0))
+        if wl.get("sliced"):
+            pfe.pfe_set_param(ctx, pfe.PFE_P_SLICE_TARGET, wl["sliced"])
         torch.cuda.synchronize()
         ev[1].record()
         lmax, _ = pfe.pfe_estimate(ctx)
         pfe.pfe_set_interval(ctx, wl["lo"] * lmax, wl["hi"] * lmax)
-        nf, _ = pfe.pfe_solve(ctx)
+        nf, _ = pfe.pfe_solve_sliced(ctx) if wl.get("sliced") else pfe.pfe_solve(ctx)
         ev[2].record()
         lam, vecs, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
         stats = pfe.pfe_get_stats(ctx)
@@ -192,6 +198,18 @@ def oracle_sample(g, stats, budget_s=20.0):
               f"Householder QR of {n}x{k} ({t_qr:.2f} s), extrapolated to the GPU solve's "
               f"{stats['matvecs']} MatVecs and ~{dense_flops:.3g} dense flops")
     return est, sample
+
+
+def max_over_ranks(values, dist, device):
+    """Max over the ranks of each timing: replicas run concurrently, so the job takes as long as its
+    slowest rank. dist None (one process) returns the values unchanged."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
 
 
 def run_reference(args, wl):
@@ -275,10 +293,7 @@ def run_native(args, wl):
     clocks = sampler.stop()
     solve_s = sum(s["solve_s"] for s in steps) / len(steps)
     e2e_s = sum(s["e2e_s"] for s in steps) / len(steps)
-    if dist is not None:
-        t = torch.tensor([solve_s, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        solve_s, e2e_s = float(t[0]), float(t[1])
+    solve_s, e2e_s = max_over_ranks([solve_s, e2e_s], dist, "cuda")
     last = steps[-1]
     # roofline of the dominant kernel (the fused filter step): FP64 is bound by the FP64 pipe
     nnzb = int(ci.size)
@@ -330,7 +345,8 @@ def run_native(args, wl):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         est, sample = oracle_sample(g, last)
         line["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
-    if rank == 0 and args.mixed and wl["precision"] == 0:
+    plain_si = wl["precision"] == 0 and wl.get("method", 0) == 0 and not wl.get("sliced")
+    if rank == 0 and args.mixed and plain_si:
         wm = dict(wl, precision=1)  # the FP64 warm-up steps above also warmed this path's set-up
         e = evs()
         sm = one_step(pfe, torch, g, rp, ci, vals, wm, e)
@@ -341,7 +357,7 @@ def run_native(args, wl):
                          "max_rel_residual": sm["max_rel_residual"],
                          "filter_f32": {"achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
                                         "peak_source": hbm_src, "shape": sm["filter_shape_f32"]}}
-    if rank == 0 and args.block_lanczos and wl["precision"] == 0:
+    if rank == 0 and args.block_lanczos and plain_si:
         wb = dict(wl, method=1)
         e = evs()
         sb = one_step(pfe, torch, g, rp, ci, vals, wb, e)

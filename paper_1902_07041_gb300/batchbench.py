@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--solo", action="store_true", help="also time the samples solved one by one")
     ap.add_argument("--threads", type=int, default=0, help="host threads for the per-sample steps (0: automatic)")
+    ap.add_argument("--method", type=int, default=0, help="0 subspace iteration (lockstep), 1 block Lanczos")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     sizes = glassgen.batch_sizes(a.samples, a.seed, a.n_min, a.n_max)
@@ -45,6 +46,7 @@ def main():
             ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
             pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, a.precision)
             pfe.pfe_set_param(ctx, pfe.PFE_P_BATCH_THREADS, a.threads)
+            pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, a.method)
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, a.lo * lmax, a.hi * lmax)
             ctxs.append(ctx)
@@ -59,7 +61,8 @@ def main():
     stats = [pfe.pfe_get_stats(c) for c in ctxs]
     for c in ctxs:
         pfe.pfe_destroy(c)
-    out = {"samples": a.samples, "atoms_total": int(sum(sizes)), "precision": a.precision, "status": st,
+    out = {"samples": a.samples, "atoms_total": int(sum(sizes)), "precision": a.precision, "method": a.method,
+           "status": st,
            "batch_s": t_batch, "batch_filter_s": stats[0]["seconds_filter"],
            "replays": stats[0]["batch_replays"], "modes_total": int(sum(nfs)),
            "iterations_max": max(s["iterations"] for s in stats), "matvecs_total": sum(s["matvecs"] for s in stats),

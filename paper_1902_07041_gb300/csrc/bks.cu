@@ -241,11 +241,11 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
         launch_bsr_step<double>(Hb, MODE_SPMM, k, ldv, Vn, nullptr, HW, nullptr, 1.0, 0.0, 0.0, 0.0, s);
         matvecs += k;
         {
-          BKS_RESERVE(double, gw2, ctx->w_gram, gram_work(n, k, k, false));
+          BKS_RESERVE(double, gw2, ctx->w_gram, std::max(gram_work(n, k, k, true), gram_work(n, k, k, false)));
           gw = gw2;  // the buffer may have grown
         }
         double *G = Tm;  // T is rebuilt by the restart below if the iteration has to continue
-        launch_gram(n, k, k, Vn, ldv, HW, ldv, 1.0, 0.0, G, k, false, gw, s);
+        launch_gram(n, k, k, Vn, ldv, HW, ldv, 1.0, 0.0, G, k, true, gw, s);  // Yw^T H Yw: symmetric
         PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k,
                                                         G, k, fin_lam, &lw));
         BKS_RESERVE(double, work2, ctx->w_cs_work, (size_t)std::max(lw, 1));

@@ -152,7 +152,8 @@ void launch_batch_step(int cpl, int blocks, const BatchDesc *desc, int32_t nsamp
 // FP64 tensor-core (DMMA) products
 // --------------------------------------------------------------------------------------
 // C (m x nn, column-major ldc) = alpha A^T B + beta C for tall row-major A (K x m), B (K x nn);
-// with sym (A == B, m == nn) only the upper tile triangle is computed and mirrored.
+// with sym (m == nn and A^T B symmetric, e.g. A == B or B = H A) only the upper tile triangle is computed
+// and mirrored.
 // work >= gram_work(K, m, nn, sym) doubles.
 int32_t gram_splits(int64_t K, int32_t m, int32_t nn, bool sym);
 size_t gram_work(int64_t K, int32_t m, int32_t nn, bool sym);

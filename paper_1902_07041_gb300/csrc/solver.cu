@@ -563,8 +563,9 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
   PFE_TRY(check_launch(ctx, "H X"));
   st.matvecs += act;
   {
-    RESERVE(double, gw, ctx->w_gram, gram_work(n, act, act, false));
-    launch_gram(n, act, act, st.X, ld, st.W, ld, 1.0, 0.0, st.A, act, false, gw, s);
+    // A = X^T H X is symmetric: only the upper tiles are computed (half the flops), then mirrored
+    RESERVE(double, gw, ctx->w_gram, gram_work(n, act, act, true));
+    launch_gram(n, act, act, st.X, ld, st.W, ld, 1.0, 0.0, st.A, act, true, gw, s);
   }
   int lw = 0;
   PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act,
@@ -1567,6 +1568,20 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
   if (cudaSetDevice(c0->device) != cudaSuccess) return pfe_fail(c0, PFE_E_CUDA, "cudaSetDevice failed");
   std::vector<pfe_status> status(nsamples, PFE_OK);
   const int32_t nthreads = c0->p_batch_threads;
+  bool all_bks = true;
+  for (int32_t i = 0; i < nsamples; ++i) all_bks = all_bks && ctxs[i]->p_method == 1;
+  if (all_bks) {
+    // block Lanczos samples: every sample's solve on its own stream, the samples concurrently from
+    // the host threads (their kernels overlap on the device); no shared graph
+    std::vector<int32_t> nf(nsamples, 0);
+    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) { status[i] = bks_solve(ctxs[i], &nf[i]); });
+    pfe_status first = PFE_OK;
+    for (int32_t i = 0; i < nsamples; ++i) {
+      if (n_found) n_found[i] = nf[i];
+      if (status[i] != PFE_OK && first == PFE_OK) first = status[i];
+    }
+    return first;
+  }
   // set-up of every sample (filter design, width, buffers, start block)
   for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) { status[i] = solve_setup(ctxs[i]); });
   BatchPlan plan;

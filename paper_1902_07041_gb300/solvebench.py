@@ -30,6 +30,9 @@ def main():
     ap.add_argument("--basis-factor", type=float, default=2.0)
     ap.add_argument("--rank1", type=int, default=1)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--filter", type=int, default=0, help="0 piecewise quadratic, 1 Dirac (with --method 1)")
+    ap.add_argument("--damping", type=int, default=0, help="0 none, 1 Jackson, 2 Lanczos")
+    ap.add_argument("--sliced", type=int, default=0, help="spectrum slicing with this many eigenvalues a slice")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
@@ -38,18 +41,24 @@ def main():
         ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
         try:
             for key, v in (("PRECISION", a.precision), ("METHOD", a.method), ("BLOCK", a.block),
-                           ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1)):
+                           ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1), ("FILTER", a.filter),
+                           ("DAMPING", a.damping)):
                 pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), v)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, a.lo * lmax, a.hi * lmax)
-            nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
+            if a.sliced > 0:
+                pfe.pfe_set_param(ctx, pfe.PFE_P_SLICE_TARGET, a.sliced)
+                nf, st = pfe.pfe_solve_sliced(ctx, raise_on_error=False)
+            else:
+                nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             stats = pfe.pfe_get_stats(ctx)
             print(json.dumps({"n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi, "method": a.method,
                               "precision": a.precision, "block": a.block, "basis_factor": a.basis_factor,
+                              "filter": a.filter, "damping": a.damping, "sliced": a.sliced,
                               "rank1_in_use": pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1), "wall_s": wall,
                               "status": st, **stats}), flush=True)
         finally:

@@ -371,6 +371,30 @@ def test_solve_batch_equals_solo(threads):
             pfe.pfe_destroy(c)
 
 
+def test_solve_batch_block_lanczos_members():
+    """A batch of block Lanczos samples (solved concurrently from host threads): exact eigenpairs."""
+    gs = [glassgen.generate(n, glassgen.subseed(5, i)) for i, n in enumerate((220, 300, 160, 260))]
+    ctxs = []
+    try:
+        for g in gs:
+            ctx, _ = make_ctx(g, METHOD=1, BLOCK=16)
+            lmax, _ = pfe.pfe_estimate(ctx)
+            pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.12 * lmax)
+            ctxs.append(ctx)
+        nfs, st = pfe.pfe_solve_batch(ctxs)
+        assert st == pfe.PFE_OK, [pfe.pfe_last_error(c) for c in ctxs]
+        for g, ctx, nf in zip(gs, ctxs, nfs):
+            lam, V, _ = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
+            lmax = pfe.pfe_get_stats(ctx)["lambda_max"]
+            H = oracle.csr_from_springs(g)
+            w, _, _ = oracle.exact_interval(H, 0.05 * lmax, 0.12 * lmax)
+            assert nf == w.size and np.allclose(lam, w, rtol=1e-10, atol=0)
+            assert np.all(oracle.residuals(H, lam, V) <= 1e-8 * lmax)
+    finally:
+        for c in ctxs:
+            pfe.pfe_destroy(c)
+
+
 def test_solve_batch_mixed_precision_members():
     """A batch whose members use different filter precisions still matches the exact eigenpairs."""
     gs = [glassgen.generate(n, 40 + i) for i, n in enumerate((200, 260))]

@@ -453,3 +453,25 @@ def test_dirac_filter_is_the_delta_projection():
     c = oracle.dirac_coeffs(g, 128, "jackson")
     assert xi < g < eta
     assert abs(oracle.series_value(c, xi) - oracle.series_value(c, eta)) <= 1e-12 * oracle.series_value(c, g)
+
+
+def test_block_lanczos_with_the_dirac_filter():
+    """The paper's production pairing (Sec. 4.1, Tables 1-3): block Lanczos on the Dirac filter rho (phi = 0.8,
+    Jackson), wanted Ritz values >= 0.9 rho(xi), then Rayleigh-Ritz with H: the exact interval eigenpairs."""
+    g = glassgen.generate(300, 5)
+    H = oracle.csr_from_springs(g)
+    th, rb, lmax = oracle.lanczos_lmax(H, 30, 0)
+    w = np.linalg.eigvalsh(H.dense())
+    a, b = 0.05 * lmax, 0.12 * lmax
+    c = d = lmax / 2
+    xi, eta = (a - c) / d, (b - c) / d
+    m = oracle.dirac_degree(xi, eta, 0.8, "jackson")
+    gm = oracle.dirac_gamma(xi, eta, m, "jackson")
+    coef = oracle.dirac_coeffs(gm, m, "jackson")
+    tau = oracle.series_value(coef, xi)
+    bks = oracle.bks_solve(H, a, b, 0.0, lmax, coef, 16, 368, 150, oracle.normal_block(0, 0, H.n, 16), 0.9 * tau,
+                           tol=1e-8, max_restarts=30)
+    sel = (w >= a) & (w <= b)
+    assert bks.status == 0 and bks.lam.size == int(sel.sum())
+    assert np.allclose(bks.lam, w[sel], rtol=1e-10, atol=0)
+    assert np.all(oracle.residuals(H, bks.lam, bks.vecs) / lmax <= 1e-8)
