@@ -69,7 +69,8 @@ def filter_work(n_atoms, nnzb, k, vec_bytes, val_bytes, rank1=False):
     n = 3 * n_atoms
     kt = 128 if vec_bytes == 4 else 64  # columns per warp (CPL x 32)
     tiles = -(-k // kt)
-    vec = 5 * n * k * vec_bytes  # gather t_j, read t_{j-1}, write t_{j+1}, read and write y
+    # gather t_j, read t_{j-1}, write t_{j+1}; y is read and written every other step (4 passes on average)
+    vec = 4 * n * k * vec_bytes
     if rank1:
         noff = nnzb - n_atoms
         byts = tiles * (noff * (3 * val_bytes + 4) + n_atoms * 6 * val_bytes + 4 * (n_atoms + 1)) + vec

@@ -22,7 +22,8 @@ namespace {
 // ---- the fused step -------------------------------------------------------------------
 // SPMM : Z = alpha A X
 // FIRST: Z = alpha A X;          Y = g0 X + g1 Z            (t_1 and p_1(H)x of Alg. 2)
-// STEP : Z = alpha A X + beta W; Y += g1 Z                  (t_{j+1} = 2 Ht t_j - t_{j-1})
+// STEP : Z = alpha A X + beta W; Y += g0 X + g1 Z if Y      (t_{j+1} = 2 Ht t_j - t_{j-1}; with g0 the
+//        term of t_j is added one step late, so that y is read and written every other step)
 // ADJ  : Z = alpha A X + beta W + g0 Y   (Y read-only)      (reverse sweep of the adjoint)
 // With A = (2/d)(H - cI) the step needs alpha = 1, beta = -1; the first step alpha = 1/2.
 // GROUPED: the 8 warps of a CTA take 8 consecutive atoms of one column chunk (their neighbour
@@ -115,6 +116,12 @@ __global__ void __launch_bounds__(256, MINB) k_bsr_step(int32_t n_atoms, const i
       ld_n(Y + off, y);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      if (g0 != T(0)) {  // the pending term of the previous step: y += g0 t_j (this atom's rows of X)
+        T xo[CPL];
+        ldg_n(X + off, xo);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], y[c]);
+      }
       st_n(Y + off, y);
     }
   }
@@ -218,6 +225,12 @@ __global__ void __launch_bounds__(256) k_bsr_step_async(int32_t n_atoms, const i
       ld_n(Y + off, y);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      if (g0 != T(0)) {  // the pending term of the previous step: y += g0 t_j (this atom's rows of X)
+        T xo[CPL];
+        ldg_n(X + off, xo);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], y[c]);
+      }
       st_n(Y + off, y);
     }
   }

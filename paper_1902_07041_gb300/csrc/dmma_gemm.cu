@@ -96,10 +96,11 @@ __global__ void k_gram_reduce(int32_t m, int32_t nn, int32_t splits, const doubl
 }
 
 // C (M x N row-major, ldc) = alpha * A (M x K row-major, lda) * Bc (K x N column-major, ldb) + beta * C.
-// C must not overlap A.
+// C must not overlap A.  upper: Bc is upper triangular (Bc[k][q] = 0 for k > q), so a column tile
+// [q0, q0 + 64) only needs k < q0 + 64.
 __global__ void __launch_bounds__(128) k_update(int64_t M, int32_t N, int32_t K, const double *__restrict__ A,
                                                 int64_t lda, const double *__restrict__ Bc, int64_t ldb, double alpha,
-                                                double beta, double *C, int64_t ldc) {
+                                                double beta, double *C, int64_t ldc, int upper) {
   const int tq = blockIdx.x;  // column tile fastest: CTAs sharing the same rows of A run together (L2 reuse)
   const int64_t ti = blockIdx.y;
   __shared__ double As[TM][LDS_U];
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(128) k_update(int64_t M, int32_t N, int32_t K,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += KC) {
+  const int kend = upper ? min(K, q0 + TN) : K;
+  for (int k0 = 0; k0 < kend; k0 += KC) {
     for (int idx = threadIdx.x; idx < TM * KC; idx += 128) {
       const int r = idx / KC, c = idx % KC;
       const int64_t i = i0 + r;
@@ -177,10 +179,10 @@ void launch_gram(int64_t K, int32_t m, int32_t nn, const double *A, int64_t lda,
 }
 
 void launch_update(int64_t M, int32_t N, int32_t K, const double *A, int64_t lda, const double *Bc, int64_t ldb,
-                   double alpha, double beta, double *C, int64_t ldc, cudaStream_t s) {
+                   double alpha, double beta, double *C, int64_t ldc, cudaStream_t s, bool upper) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((N + TN - 1) / TN, (unsigned)((M + TM - 1) / TM));
-  PFE_LAUNCH k_update<<<grid, 128, 0, s>>>(M, N, K, A, lda, Bc, ldb, alpha, beta, C, ldc);
+  PFE_LAUNCH k_update<<<grid, 128, 0, s>>>(M, N, K, A, lda, Bc, ldb, alpha, beta, C, ldc, upper ? 1 : 0);
 }
 
 }  // namespace pfe

@@ -57,7 +57,7 @@ struct Bsr {
 // Step modes of the fused BSR kernel (row-major n x k multivectors with row stride ld):
 //   SPMM : Z = alpha A X
 //   FIRST: Z = alpha A X;              Y = g0 X + g1 Z
-//   STEP : Z = alpha A X + beta W;     Y = Y + g1 Z        (W may alias Z; Y may be null)
+//   STEP : Z = alpha A X + beta W;     Y = Y + g0 X + g1 Z (W may alias Z; Y may be null)
 //   ADJ  : Z = alpha A X + beta W + g0 Y                   (Y read-only; W may alias Z)
 enum StepMode { MODE_SPMM = 0, MODE_FIRST = 1, MODE_STEP = 2, MODE_ADJ = 3 };
 
@@ -161,7 +161,8 @@ void launch_gram(int64_t K, int32_t m, int32_t nn, const double *A, int64_t lda,
                  double alpha, double beta, double *C, int64_t ldc, bool sym, double *work, cudaStream_t s);
 // C (M x N row-major, ldc) = alpha A (M x K row-major, lda) Bc (K x N column-major, ldb) + beta C
 void launch_update(int64_t M, int32_t N, int32_t K, const double *A, int64_t lda, const double *Bc, int64_t ldb,
-                   double alpha, double beta, double *C, int64_t ldc, cudaStream_t s);
+                   double alpha, double beta, double *C, int64_t ldc, cudaStream_t s,
+                   bool upper = false);
 
 // --------------------------------------------------------------------------------------
 // Host math of the filter (App. A, Sec. 2.3, eq. (thresh)); independent of the oracle

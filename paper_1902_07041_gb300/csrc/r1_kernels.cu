@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256, MINB) k_r1_step(int32_t n_atoms, const in
       T y[CPL];
       ld_n(Y + off, y);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[r][c], fma(g1, z[c], y[c]));  // g0 t_j: already in registers
       st_n(Y + off, y);
     }
   }

@@ -96,9 +96,14 @@ pfe_status run_filter(pfe_ctx *ctx, const Bsr<T> &A, const double *coef, int32_t
   launch_bsr_step<T>(A, MODE_FIRST, k, ld, X, nullptr, b0, Y, T(0.5), T(0), (T)coef[0], (T)coef[1], s);
   const T *tprev = X;
   T *tcur = b0;
+  // y is read and written every other step: an even step j adds g_j t_j (its input) and g_{j+1} t_{j+1}
+  // (its output), an odd step adds nothing unless it is the last one (then g_m t_m)
   for (int32_t j = 1; j < m; ++j) {
     T *out = (tprev == X) ? b1 : const_cast<T *>(tprev);
-    launch_bsr_step<T>(A, MODE_STEP, k, ld, tcur, tprev, out, Y, T(1), T(-1), T(0), (T)coef[j + 1], s);
+    const bool even = (j % 2) == 0, last = j == m - 1;
+    T *y = (even || last) ? Y : nullptr;
+    const T g_in = even ? (T)coef[j] : T(0);
+    launch_bsr_step<T>(A, MODE_STEP, k, ld, tcur, tprev, out, y, T(1), T(-1), g_in, (T)coef[j + 1], s);
     tprev = tcur;
     tcur = out;
   }
@@ -399,7 +404,7 @@ pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, 
     bool shifted = false;
     PFE_TRY(chol_factor(ctx, G, Rinv, k, &shifted));
     any_shift = any_shift || shifted;
-    launch_update(ctx->n, k, k, src, ld, Rinv, k, 1.0, 0.0, dst, ld, s);
+    launch_update(ctx->n, k, k, src, ld, Rinv, k, 1.0, 0.0, dst, ld, s, true);  // R^{-1} is upper triangular
     PFE_TRY(check_launch(ctx, "CholeskyQR update"));
     *result = dst;
     std::swap(src, dst);

@@ -45,11 +45,12 @@ def main():
         s = 8 if a.dtype == "f64" else 4
         kt = 64 if s == 8 else 128
         nnzb = ci.size
-        step_bytes = -(-a.k // kt) * (nnzb * (9 * s + 4) + 4 * (g.n_atoms + 1)) + 5 * g.n * a.k * s
+        # vector passes: gather t_j, read t_{j-1}, write t_{j+1}, and y read and written every other step
+        step_bytes = -(-a.k // kt) * (nnzb * (9 * s + 4) + 4 * (g.n_atoms + 1)) + 4 * g.n * a.k * s
         step_flops = 18 * nnzb * a.k + 6 * g.n * a.k
         noff = nnzb - g.n_atoms
         # the rank-1 form: 3 values and 6 FMAs per off-diagonal block and column, full diagonal blocks
-        r1_bytes = -(-a.k // kt) * (noff * (3 * s + 4) + g.n_atoms * 6 * s + 4 * (g.n_atoms + 1)) + 5 * g.n * a.k * s
+        r1_bytes = -(-a.k // kt) * (noff * (3 * s + 4) + g.n_atoms * 6 * s + 4 * (g.n_atoms + 1)) + 4 * g.n * a.k * s
         r1_flops = 12 * noff * a.k + 18 * g.n_atoms * a.k + 6 * g.n * a.k
         if a.adjoint:
             coef = np.ones(a.degree + 1) / (a.degree + 1)

@@ -231,7 +231,8 @@ def test_spectrum_slicing_edges_on_eigenvalues():
     sel = np.sort(full[(full >= a) & (full <= b)])
     assert st == pfe.PFE_OK and stats["slices"] == 3
     assert nf == sel.size and np.allclose(lam, sel, rtol=0, atol=1e-12)
-    assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-8
+    # vectors from different slices: orthogonal to residual / gap (1e-8 lambda_max / 1.6e-3 here)
+    assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-5
     # the double eigenvalue's two vectors span the coordinates 300 and 301
     j = np.nonzero(np.abs(lam - 0.5) < 1e-9)[0]
     assert j.size == 2 and np.allclose(np.linalg.norm(V[[300, 301]][:, j], axis=0), 1.0, atol=1e-8)
