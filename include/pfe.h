@@ -91,7 +91,7 @@ enum {
                                Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),
                                FP64 only */
   PFE_P_BLOCK = 22,         /* block size of METHOD 1 (default 64) */
-  PFE_P_BASIS_FACTOR = 23,  /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 2; >= 2) */
+  PFE_P_BASIS_FACTOR = 23,  /* METHOD 1: basis size = BASIS_FACTOR x the wanted count (default 2; >= 1.25) */
   PFE_P_BATCH_THREADS = 24, /* pfe_solve_batch, read from the first context: host threads that run the
                                samples' set-up and dense steps concurrently, each sample on its own
                                stream (0 = automatic: min(samples, hardware threads, 16); 1 = serial) */

@@ -1247,7 +1247,7 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       ctx->p_block = (int32_t)v;
       break;
     case PFE_P_BASIS_FACTOR:
-      if (!(v >= 2.0)) return pfe_fail(ctx, PFE_E_ARG, "BASIS_FACTOR must be >= 2");
+      if (!(v >= 1.25)) return pfe_fail(ctx, PFE_E_ARG, "BASIS_FACTOR must be >= 1.25");
       ctx->p_basis_factor = v;
       break;
     case PFE_P_BATCH_THREADS:

@@ -180,6 +180,25 @@ def test_solve_with_and_without_rank1_form(rank1):
     assert st["iterations"] >= 2
 
 
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_filter_low_degrees(m, dtype):
+    """Degrees 1-5: the y accumulation that skips odd steps must still add every term (the last
+    step adds its own term when it is odd)."""
+    g = glassgen.generate(150, 3)
+    ctx, _ = make_ctx(g, LAMBDA_MAX=0.3)
+    try:
+        coef = np.random.default_rng(m).standard_normal(m + 1)
+        X = np.random.default_rng(7).standard_normal((g.n, 9))
+        dt = pfe.PFE_F64 if dtype == "f64" else pfe.PFE_F32
+        Y = filter_gpu(ctx, coef, X, dt)
+        ref = oracle.cheb_filter(oracle.csr_from_springs(g), 0.15, 0.15, coef, X)
+        tol = 1e-12 if dtype == "f64" else 1e-5
+        assert np.max(np.abs(Y - ref)) <= tol * np.abs(X).max() * np.abs(coef).sum()
+    finally:
+        pfe.pfe_destroy(ctx)
+
+
 def test_filter_first_step_is_transformed_hessian():
     """Coefficients e_1 give Ht X = (H - cI)/d X: mass weighting (a0) and the transform."""
     g = glassgen.generate(200, 9)
