@@ -33,6 +33,8 @@ def main():
     ap.add_argument("--filter", type=int, default=0, help="0 piecewise quadratic, 1 Dirac (with --method 1)")
     ap.add_argument("--damping", type=int, default=0, help="0 none, 1 Jackson, 2 Lanczos")
     ap.add_argument("--sliced", type=int, default=0, help="spectrum slicing with this many eigenvalues a slice")
+    ap.add_argument("--rate", type=float, default=0.1 ** 0.5, help="r of eq. (thresh) (piecewise quadratic filter)")
+    ap.add_argument("--phi", type=float, default=0.8, help="phi of the Dirac filter")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
@@ -42,7 +44,7 @@ def main():
         try:
             for key, v in (("PRECISION", a.precision), ("METHOD", a.method), ("BLOCK", a.block),
                            ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1), ("FILTER", a.filter),
-                           ("DAMPING", a.damping)):
+                           ("DAMPING", a.damping), ("RATE", a.rate), ("PHI", a.phi)):
                 pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), v)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -58,7 +60,8 @@ def main():
             stats = pfe.pfe_get_stats(ctx)
             print(json.dumps({"n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi, "method": a.method,
                               "precision": a.precision, "block": a.block, "basis_factor": a.basis_factor,
-                              "filter": a.filter, "damping": a.damping, "sliced": a.sliced,
+                              "filter": a.filter, "damping": a.damping, "sliced": a.sliced, "rate": a.rate,
+                              "phi": a.phi,
                               "rank1_in_use": pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1), "wall_s": wall,
                               "status": st, **stats}), flush=True)
         finally:
