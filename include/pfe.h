@@ -62,7 +62,8 @@ typedef enum {
 enum {
   PFE_P_DEGREE = 1,         /* filter degree m; 0 = choose by eq. (thresh) (default 0) */
   PFE_P_EPS_FRAC = 2,       /* margin eps as a fraction of eta - xi (default 0.25) */
-  PFE_P_RATE = 3,           /* convergence rate r of eq. (thresh) (default sqrt(0.1)) */
+  PFE_P_RATE = 3,           /* convergence rate r of eq. (thresh) (default sqrt(0.1) for the subspace
+                               iteration, 0.1^(1/4) for block Lanczos, METHOD 1) */
   PFE_P_DAMPING = 4,        /* 0 none (default, best for subspace iteration in Sec. 4.1), 1 Jackson, 2 Lanczos sigma */
   PFE_P_WIDTH = 5,          /* subspace width q; 0 = max(WIDTH_FACTOR * count estimate, 1.1 * window count
                                estimate + 8, MIN_WIDTH), the window being [a - eps, b + eps] (default 0) */

@@ -103,7 +103,7 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   // wanted Ritz values of Op: piecewise quadratic filter, theta >= sqrt(r) min(p(xi), p(eta)); Dirac
   // filter, theta >= DIRAC_CUT x tau with tau = rho(xi) = rho(eta)
   const double pe = std::min(chebyshev_value(ctx->coef, ctx->m, ctx->xi), chebyshev_value(ctx->coef, ctx->m, ctx->eta));
-  const double theta_cut = (ctx->p_filter == 1) ? ctx->p_dirac_cut * ctx->dirac_tau : std::sqrt(ctx->p_rate) * pe;
+  const double theta_cut = (ctx->p_filter == 1) ? ctx->p_dirac_cut * ctx->dirac_tau : std::sqrt(ctx->rate_of()) * pe;
   // n x ldv buffers: V (basis), Vn (next basis, or the wanted Ritz vectors), HW (products with H),
   // Z = ctx->L (the returned eigenvectors)
   BKS_RESERVE(double, V, ctx->w_bks[0], (size_t)n * ldv);

@@ -22,8 +22,9 @@ namespace {
 // ---- the fused step -------------------------------------------------------------------
 // SPMM : Z = alpha A X
 // FIRST: Z = alpha A X;          Y = g0 X + g1 Z            (t_1 and p_1(H)x of Alg. 2)
-// STEP : Z = alpha A X + beta W; Y += g0 X + g1 Z if Y      (t_{j+1} = 2 Ht t_j - t_{j-1}; with g0 the
-//        term of t_j is added one step late, so that y is read and written every other step)
+// STEP : Z = alpha A X + beta W; Y += g1 Z if Y            (t_{j+1} = 2 Ht t_j - t_{j-1})
+// STEP_ACC: as STEP with Y += g0 X + g1 Z                   (the term of t_j added one step late, so
+//        that y is read and written every other step)
 // ADJ  : Z = alpha A X + beta W + g0 Y   (Y read-only)      (reverse sweep of the adjoint)
 // With A = (2/d)(H - cI) the step needs alpha = 1, beta = -1; the first step alpha = 1/2.
 // GROUPED: the 8 warps of a CTA take 8 consecutive atoms of one column chunk (their neighbour
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(256, MINB) k_bsr_step(int32_t n_atoms, const i
     T z[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) z[c] = alpha * acc[r][c];
-    if (MODE == MODE_STEP || MODE == MODE_ADJ) {
+    if (MODE == MODE_STEP || MODE == MODE_STEP_ACC || MODE == MODE_ADJ) {
       T w[CPL];
       ld_n(W + off, w);
 #pragma unroll
@@ -116,12 +117,13 @@ __global__ void __launch_bounds__(256, MINB) k_bsr_step(int32_t n_atoms, const i
       ld_n(Y + off, y);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
-      if (g0 != T(0)) {  // the pending term of the previous step: y += g0 t_j (this atom's rows of X)
-        T xo[CPL];
-        ldg_n(X + off, xo);
+      st_n(Y + off, y);
+    } else if (MODE == MODE_STEP_ACC) {  // also the pending term g0 t_j (this atom's rows of X)
+      T y[CPL], xo[CPL];
+      ld_n(Y + off, y);
+      ldg_n(X + off, xo);
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], y[c]);
-      }
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], fma(g1, z[c], y[c]));
       st_n(Y + off, y);
     }
   }
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(256) k_bsr_step_async(int32_t n_atoms, const i
     T z[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) z[c] = alpha * acc[r][c];
-    if (MODE == MODE_STEP || MODE == MODE_ADJ) {
+    if (MODE == MODE_STEP || MODE == MODE_STEP_ACC || MODE == MODE_ADJ) {
       T w[CPL];
       ld_n(W + off, w);
 #pragma unroll
@@ -225,12 +227,13 @@ __global__ void __launch_bounds__(256) k_bsr_step_async(int32_t n_atoms, const i
       ld_n(Y + off, y);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
-      if (g0 != T(0)) {  // the pending term of the previous step: y += g0 t_j (this atom's rows of X)
-        T xo[CPL];
-        ldg_n(X + off, xo);
+      st_n(Y + off, y);
+    } else if (MODE == MODE_STEP_ACC) {  // also the pending term g0 t_j (this atom's rows of X)
+      T y[CPL], xo[CPL];
+      ld_n(Y + off, y);
+      ldg_n(X + off, xo);
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], y[c]);
-      }
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[c], fma(g1, z[c], y[c]));
       st_n(Y + off, y);
     }
   }
@@ -250,6 +253,8 @@ void dispatch_async(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X
     PFE_ASYNC_LAUNCH(MODE_FIRST);
   else if (mode == MODE_ADJ)
     PFE_ASYNC_LAUNCH(MODE_ADJ);
+  else if (mode == MODE_STEP_ACC)
+    PFE_ASYNC_LAUNCH(MODE_STEP_ACC);
   else
     PFE_ASYNC_LAUNCH(MODE_STEP);
 #undef PFE_ASYNC_LAUNCH
@@ -270,6 +275,8 @@ void dispatch_mode(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X,
     PFE_STEP_LAUNCH(MODE_FIRST);
   else if (mode == MODE_ADJ)
     PFE_STEP_LAUNCH(MODE_ADJ);
+  else if (mode == MODE_STEP_ACC)
+    PFE_STEP_LAUNCH(MODE_STEP_ACC);
   else
     PFE_STEP_LAUNCH(MODE_STEP);
 #undef PFE_STEP_LAUNCH
@@ -424,7 +431,7 @@ void launch_bsr_step<double>(const Bsr<double> &A, int mode, int32_t k, int64_t 
   const bool al16 = aligned(X, 16) && aligned(W, 16) && aligned(Z, 16) && aligned(Y, 16);
   const int cpl = cpl_for<double>(k, ld, al16, false);
   const int v = pick_variant(0, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
-  if (mode == MODE_FIRST || mode == MODE_STEP) g_last_variant[0].store((v >= kVariants && !A.u) ? 0 : v);
+  if (mode == MODE_FIRST || mode == MODE_STEP || mode == MODE_STEP_ACC) g_last_variant[0].store((v >= kVariants && !A.u) ? 0 : v);
   dispatch_cpl<double>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 
@@ -436,7 +443,7 @@ void launch_bsr_step<float>(const Bsr<float> &A, int mode, int32_t k, int64_t ld
   const bool al8 = aligned(X, 8) && aligned(W, 8) && aligned(Z, 8) && aligned(Y, 8);
   const int cpl = cpl_for<float>(k, ld, al16, al8);
   const int v = pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), A.u != nullptr);
-  if (mode == MODE_FIRST || mode == MODE_STEP) g_last_variant[1].store((v >= kVariants && !A.u) ? 0 : v);
+  if (mode == MODE_FIRST || mode == MODE_STEP || mode == MODE_STEP_ACC) g_last_variant[1].store((v >= kVariants && !A.u) ? 0 : v);
   dispatch_cpl<float>(cpl, v, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
 }
 

@@ -57,9 +57,10 @@ struct Bsr {
 // Step modes of the fused BSR kernel (row-major n x k multivectors with row stride ld):
 //   SPMM : Z = alpha A X
 //   FIRST: Z = alpha A X;              Y = g0 X + g1 Z
-//   STEP : Z = alpha A X + beta W;     Y = Y + g0 X + g1 Z (W may alias Z; Y may be null)
+//   STEP : Z = alpha A X + beta W;     Y = Y + g1 Z        (W may alias Z; Y may be null)
+//   STEP_ACC: as STEP with Y = Y + g0 X + g1 Z  (the term of X added one step late)
 //   ADJ  : Z = alpha A X + beta W + g0 Y                   (Y read-only; W may alias Z)
-enum StepMode { MODE_SPMM = 0, MODE_FIRST = 1, MODE_STEP = 2, MODE_ADJ = 3 };
+enum StepMode { MODE_SPMM = 0, MODE_FIRST = 1, MODE_STEP = 2, MODE_ADJ = 3, MODE_STEP_ACC = 4 };
 
 template <typename T>
 void launch_bsr_step(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z, T *Y, T alpha,
@@ -231,7 +232,10 @@ struct pfe_ctx {
   // parameters
   int32_t p_degree = 0;
   double p_eps_frac = 0.25;
-  double p_rate = 0.31622776601683794;
+  double p_rate = 0.0;  // 0: the method's default (rate_of)
+  // r of eq. (thresh): the set value, else sqrt(0.1) for the subspace iteration (the locking paragraph
+  // after Alg. 4) and 0.1^(1/4) for block Lanczos (its best piecewise-quadratic choice in Tables 1-3)
+  double rate_of() const { return p_rate > 0.0 ? p_rate : (p_method == 1 ? 0.5623413251903491 : 0.31622776601683794); }
   int p_damping = 0;
   int32_t p_width = 0;
   double p_width_factor = 1.5;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256, MINB) k_r1_step(int32_t n_atoms, const in
     T z[CPL];
 #pragma unroll
     for (int c = 0; c < CPL; ++c) z[c] = alpha * acc[r][c];
-    if (MODE == MODE_STEP || MODE == MODE_ADJ) {
+    if (MODE == MODE_STEP || MODE == MODE_STEP_ACC || MODE == MODE_ADJ) {
       T w[CPL];
       ld_n(W + off, w);
 #pragma unroll
@@ -111,7 +111,16 @@ __global__ void __launch_bounds__(256, MINB) k_r1_step(int32_t n_atoms, const in
       T y[CPL];
       ld_n(Y + off, y);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) y[c] = fma(g0, xo[r][c], fma(g1, z[c], y[c]));  // g0 t_j: already in registers
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g1, z[c], y[c]);
+      st_n(Y + off, y);
+    } else if (MODE == MODE_STEP_ACC) {
+      // also the pending term g0 t_j: this atom's rows of X again (cache hits), so that they need
+      // not stay in registers through the neighbour loop
+      T y[CPL], x[CPL];
+      ld_n(Y + off, y);
+      ldg_n(X + off, x);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) y[c] = fma(g0, x[c], fma(g1, z[c], y[c]));
       st_n(Y + off, y);
     }
   }
@@ -131,6 +140,8 @@ void dispatch_r1_mode(const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T 
     PFE_R1_LAUNCH(MODE_FIRST);
   else if (mode == MODE_ADJ)
     PFE_R1_LAUNCH(MODE_ADJ);
+  else if (mode == MODE_STEP_ACC)
+    PFE_R1_LAUNCH(MODE_STEP_ACC);
   else
     PFE_R1_LAUNCH(MODE_STEP);
 #undef PFE_R1_LAUNCH

@@ -101,9 +101,11 @@ pfe_status run_filter(pfe_ctx *ctx, const Bsr<T> &A, const double *coef, int32_t
   for (int32_t j = 1; j < m; ++j) {
     T *out = (tprev == X) ? b1 : const_cast<T *>(tprev);
     const bool even = (j % 2) == 0, last = j == m - 1;
-    T *y = (even || last) ? Y : nullptr;
-    const T g_in = even ? (T)coef[j] : T(0);
-    launch_bsr_step<T>(A, MODE_STEP, k, ld, tcur, tprev, out, y, T(1), T(-1), g_in, (T)coef[j + 1], s);
+    if (even)
+      launch_bsr_step<T>(A, MODE_STEP_ACC, k, ld, tcur, tprev, out, Y, T(1), T(-1), (T)coef[j], (T)coef[j + 1], s);
+    else
+      launch_bsr_step<T>(A, MODE_STEP, k, ld, tcur, tprev, out, last ? Y : nullptr, T(1), T(-1), T(0),
+                         (T)coef[j + 1], s);
     tprev = tcur;
     tcur = out;
   }
@@ -263,7 +265,7 @@ pfe_status ensure_filter(pfe_ctx *ctx) {
     return PFE_OK;
   }
   if (m <= 0) {
-    m = choose_degree(ctx->xi, ctx->eta, ctx->eps, ctx->p_rate, ctx->p_damping, 60000);
+    m = choose_degree(ctx->xi, ctx->eta, ctx->eps, ctx->rate_of(), ctx->p_damping, 60000);
     if (m < 0) return pfe_fail(ctx, PFE_E_ARG, "no filter degree <= 60000 meets the rate; widen eps or r");
   }
   std::vector<double> gam, g;
@@ -1241,6 +1243,7 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
     case PFE_P_METHOD:
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "METHOD must be 0 or 1");
       ctx->p_method = (int)v;
+      if (ctx->p_rate <= 0.0) ctx->has_filter = false;  // the default rate depends on the method
       break;
     case PFE_P_BLOCK:
       if (!int_ok(1) || v > 4096) return pfe_fail(ctx, PFE_E_ARG, "BLOCK must be an integer in [1, 4096]");
@@ -1294,7 +1297,7 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
   switch (key) {
     case PFE_P_DEGREE: *v = ctx->p_degree; break;
     case PFE_P_EPS_FRAC: *v = ctx->p_eps_frac; break;
-    case PFE_P_RATE: *v = ctx->p_rate; break;
+    case PFE_P_RATE: *v = ctx->rate_of(); break;
     case PFE_P_DAMPING: *v = ctx->p_damping; break;
     case PFE_P_WIDTH: *v = ctx->p_width; break;
     case PFE_P_WIDTH_FACTOR: *v = ctx->p_width_factor; break;
