@@ -43,11 +43,12 @@ WORKLOADS = {
 DEFAULT = "glass-n100k-fp64"
 
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
-# DRAM traffic / algorithmic bytes of the fused step, from one ncu capture per form and type
+# DRAM traffic / algorithmic bytes of the fused step, from ncu captures per form and type
 # (N = 100,000; k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md, filter_step_f32_n100k.md,
-# filter_step_r1_f64_n100k.md, filter_step_r1_f32_n100k.md)
+# filter_step_r1_f64_n100k.md, filter_step_r1_f32_n100k.md; the rank-1 figures are the mean of a
+# STEP and a STEP_ACC launch, which the filter alternates)
 TRAFFIC_RATIO = {("bsr", 8): 872.490752 / 854.171476, ("bsr", 4): 830.966784 / 813.542884,
-                 ("rank1", 8): 818.178048 / 802.000020, ("rank1", 4): 800.012800 / 787.257156}
+                 ("rank1", 8): 663.502336 / 648.400020, ("rank1", 4): 645.863808 / 633.657156}
 R1_SHAPES = (7, 8, 9)  # kernel shapes of the fused step that run on the rank-1 form
 
 
@@ -315,7 +316,7 @@ def run_native(args, wl):
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": ratio * bl if ratio else None,
                 "traffic_note": ("bytes per average launch: algorithmic x the ncu-measured DRAM/algorithmic "
-                                 "ratio of the k = 64 capture") if ratio else "no ncu capture of this kernel yet",
+                                 "ratio of the k = 64 captures") if ratio else "no ncu capture of this kernel yet",
                 "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
                 "filter_gbs_fp64": (b1 / last["width"]) * last["filter_col_steps"] / secs64 / 1e9,
                 "launches": last["filter_launches"], "operator_form": form}
