@@ -1582,7 +1582,25 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     // block Lanczos samples: every sample's solve on its own stream, the samples concurrently from
     // the host threads (their kernels overlap on the device); no shared graph
     std::vector<int32_t> nf(nsamples, 0);
-    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) { status[i] = bks_solve(ctxs[i], &nf[i]); });
+    // each sample's work buffers (several n x basis blocks) are released when its solve ends, so that
+    // only the solves in flight hold them; a sample that found no room beside the others runs again
+    // afterwards, one at a time
+    auto release_work = [](pfe_ctx *c) {
+      for (DBuf *b : {&c->w_X, &c->w_Y, &c->w_W, &c->w_T0, &c->w_T1, &c->w_T2, &c->w_small, &c->w_small2, &c->w_red,
+                      &c->w_cs_work, &c->w_ckpt, &c->w_rr, &c->w_gram, &c->w_bks[0], &c->w_bks[1], &c->w_bks[2],
+                      &c->w_bks[3], &c->w_bks[4]})
+        dbuf_free(*b);
+    };
+    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) {
+      status[i] = bks_solve(ctxs[i], &nf[i]);
+      release_work(ctxs[i]);
+    });
+    for (int32_t i = 0; i < nsamples; ++i) {
+      if (status[i] != PFE_E_NOMEM) continue;
+      cudaGetLastError();  // the failed allocation's error state
+      status[i] = bks_solve(ctxs[i], &nf[i]);
+      release_work(ctxs[i]);
+    }
     pfe_status first = PFE_OK;
     for (int32_t i = 0; i < nsamples; ++i) {
       if (n_found) n_found[i] = nf[i];
