@@ -132,9 +132,18 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   const int max_restarts = std::max(ctx->p_max_iters, 1);
   double tol_op = 1e-10, t_filter = 0.0, t_orth = 0.0, t_rr = 0.0;
   int64_t matvecs = 0, f_launch = 0, f_cols = 0;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  struct Events {  // destroyed on every return path
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Events() {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+    }
+    ~Events() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } events;
+  cudaEvent_t e0 = events.e0, e1 = events.e1;
   auto timed = [&](double &acc) {
     float ms = 0;
     cudaEventRecord(e1, s);
@@ -303,8 +312,6 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
     nv = keep;
     timed(t_orth);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   // results: columns of Z (= ctx->L) in ascending eigenvalue order (syevd returns ascending)
   ctx->ldq = ldv;
   ctx->result_cols = sel_cols;
