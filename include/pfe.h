@@ -161,6 +161,18 @@ pfe_status pfe_estimate(pfe_ctx *ctx, double *lambda_max, double *count_est);
  * lambda_max step first if needed.  PFE_E_CAPACITY if cap < m + 1 (m still stored). */
 pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs, double *c, double *d);
 
+/* The same filter design without a context (host computation only; no GPU needed), on the
+ * transformed interval [xi, eta] within [-1, 1]:
+ *   kind 0: the piecewise quadratic filter of eq. (fct_f) with margin eps and rate r (eq. (thresh));
+ *   kind 1: the Dirac filter of eq. (cheby-delta.1), centred so that rho(xi) = rho(eta), with phi;
+ * damping 0 none, 1 Jackson, 2 Lanczos (Sec. 2.3).  degree 0: the automatic degree (smallest
+ * qualifying, as the solver picks it), else that degree.  *m_out receives the degree;
+ * coeffs[0..m] (host, cap doubles; may be NULL to query m) the damped Chebyshev coefficients.
+ * PFE_E_ARG for an invalid interval or parameter or when no degree <= 60000 qualifies;
+ * PFE_E_CAPACITY if cap < m + 1 (m still stored). */
+pfe_status pfe_design_filter(int kind, double xi, double eta, double eps, double r, double phi, int damping,
+                             int32_t degree, int32_t cap, int32_t *m_out, double *coeffs);
+
 /* Alg. 3, solve step: compute all eigenpairs with lambda in [a, b] by filtered subspace iteration
  * (Alg. 4 with Rayleigh-Ritz on H every iteration, CholQR2 orthonormalisation, locking), or with
  * PFE_P_METHOD = 1 by thick-restart block Lanczos on p(Ht) followed by Rayleigh-Ritz with H.

@@ -41,7 +41,7 @@ EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", 
            "pfe_get_param", "pfe_set_interval", "pfe_estimate", "pfe_get_filter", "pfe_solve",
            "pfe_get_eigenpairs", "pfe_get_stats", "pfe_filter_apply", "pfe_filter_adjoint",
            "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc", "pfe_participation_ratio",
-           "pfe_plane_wave_content", "pfe_solve_sliced")
+           "pfe_plane_wave_content", "pfe_solve_sliced", "pfe_design_filter")
 
 
 class PfeError(RuntimeError):
@@ -101,6 +101,7 @@ def load(path: str | None = None):
         "pfe_participation_ratio": (ctypes.c_int, [_P, _I32, _P]),
         "pfe_plane_wave_content": (ctypes.c_int, [_P, _P, _I32, _P, _I32, _P]),
         "pfe_solve_sliced": (ctypes.c_int, [_P, _I32, _P, _P]),
+        "pfe_design_filter": (ctypes.c_int, [ctypes.c_int, _D, _D, _D, _D, _D, ctypes.c_int, _I32, _I32, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -327,3 +328,21 @@ def pfe_solve_sliced(ctx, edges=None, raise_on_error=True):
     if raise_on_error and st != PFE_OK:
         _check(st, ctx)
     return nf.value, st
+
+
+DAMPING_KINDS = {"none": 0, "jackson": 1, "lanczos": 2}
+
+
+def pfe_design_filter(kind, xi, eta, eps=0.0, r=0.0, phi=0.0, damping="none", degree=0):
+    """Filter design on the host (no context, no GPU): kind "pq" (eps, r) or "dirac" (phi).
+    Returns (degree, damped Chebyshev coefficients)."""
+    k = {"pq": 0, "dirac": 1}[kind]
+    dmp = DAMPING_KINDS[damping] if isinstance(damping, str) else int(damping)
+    m = ctypes.c_int32(0)
+    _check(load().pfe_design_filter(k, float(xi), float(eta), float(eps), float(r), float(phi), dmp, int(degree), 0,
+                                    ctypes.byref(m), None), None, "pfe_design_filter: invalid arguments")
+    c = np.zeros(m.value + 1)
+    _check(load().pfe_design_filter(k, float(xi), float(eta), float(eps), float(r), float(phi), dmp, int(degree),
+                                    c.size, ctypes.byref(m), c.ctypes.data), None, "pfe_design_filter failed")
+    return m.value, c
+

@@ -248,3 +248,35 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
 }
 
 }  // namespace pfe
+
+// ---- the filter design without a context (host only, callable without a GPU)
+extern "C" pfe_status pfe_design_filter(int kind, double xi, double eta, double eps, double r, double phi, int damping,
+                                        int32_t degree, int32_t cap, int32_t *m_out, double *coeffs) {
+  using namespace pfe;
+  if (!m_out || (kind != 0 && kind != 1) || (damping < 0 || damping > 2) || degree < 0) return PFE_E_ARG;
+  if (!(xi >= -1.0 && xi < eta && eta <= 1.0)) return PFE_E_ARG;
+  if (kind == 0 && !(eps > 0.0 && r > 0.0 && r < 1.0)) return PFE_E_ARG;
+  if (kind == 1 && !(phi > 0.0 && phi < 1.0)) return PFE_E_ARG;
+  int32_t m = degree;
+  if (m == 0) {
+    m = (kind == 0) ? choose_degree(xi, eta, eps, r, damping, 60000) : choose_dirac_degree(xi, eta, phi, damping, 60000);
+    if (m < 0) return PFE_E_ARG;
+  }
+  *m_out = m;
+  if (!coeffs) return PFE_OK;
+  if (cap < m + 1) return PFE_E_CAPACITY;
+  std::vector<double> c;
+  if (kind == 0) {
+    std::vector<double> gam, g;
+    pq_coefficients(xi, eta, eps, m, gam);
+    damping_factors(damping, m, g);
+    c.resize((size_t)m + 1);
+    for (int32_t j = 0; j <= m; ++j) c[j] = gam[j] * g[j];
+  } else {
+    c.resize((size_t)m + 1);
+    dirac_coefficients(dirac_center(xi, eta, m, damping), m, damping, c);
+  }
+  std::copy(c.begin(), c.end(), coeffs);
+  return PFE_OK;
+}
+

@@ -113,3 +113,51 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.pfe_set_interval(None, 0.0, 1.0) == pfe.PFE_E_ARG
     assert lib.pfe_solve(None, None) == pfe.PFE_E_ARG
     lib.pfe_destroy(None)
+
+
+_RATES = {"0.1": 0.1, "sqrt(0.1)": 0.1 ** 0.5, "0.1^(1/4)": 0.1 ** 0.25}
+
+
+def test_library_filter_design_reproduces_tables_1_3(lib, golden):
+    """The library's own degree selection (host code of libpfe.so, no GPU): all 27 piecewise-quadratic
+    and all 18 Dirac degrees that Tables 1-3 print."""
+    pq = golden("degrees_tables_1_3.json")
+    for case in pq["cases"]:
+        for i, rname in enumerate(pq["rows_r"]):
+            for j, kind in enumerate(pq["columns"]):
+                m, _ = pfe.pfe_design_filter("pq", case["xi"], case["eta"], eps=case["eps"], r=_RATES[rname],
+                                             damping=kind)
+                assert m == case["degrees"][i][j], (case["table"], rname, kind, m)
+    dr = golden("dirac_degrees_tables_1_3.json")
+    for case in dr["cases"]:
+        for i, phi in enumerate(dr["rows_phi"]):
+            for j, kind in enumerate(dr["columns"]):
+                m, _ = pfe.pfe_design_filter("dirac", case["xi"], case["eta"], phi=phi, damping=kind)
+                assert m == case["degrees"][i][j], (case["table"], phi, kind, m)
+
+
+@pytest.mark.parametrize("kind", ["none", "jackson", "lanczos"])
+def test_library_filter_coefficients_match_oracle(lib, kind):
+    """Coefficients of both filters at a fixed degree against the oracle's independent routines."""
+    xi, eta, eps = -0.9, -0.885, 0.002
+    m, c = pfe.pfe_design_filter("pq", xi, eta, eps=eps, r=0.3, damping=kind, degree=150)
+    assert m == 150
+    ref = oracle.filter_coeffs(xi, eta, eps, 150, kind)
+    # the two sides evaluate the App. A integrals independently: agreement to ~1e-11 of the largest
+    # coefficient (sin(l arccos x) at l = 150 amplifies rounding of arccos by ~l / sqrt(1 - x^2))
+    assert np.allclose(c, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    m, c = pfe.pfe_design_filter("dirac", xi, eta, phi=0.8, damping=kind, degree=120)
+    g = oracle.dirac_gamma(xi, eta, 120, kind)
+    ref = oracle.dirac_coeffs(g, 120, kind)
+    assert np.allclose(c, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    # the Dirac filter is balanced: equal values at the interval edges
+    assert abs(oracle.series_value(c, xi) - oracle.series_value(c, eta)) <= 1e-10 * np.abs(c).sum()
+
+
+def test_library_filter_design_rejects_bad_input(lib):
+    with pytest.raises(pfe.PfeError):
+        pfe.pfe_design_filter("pq", -0.8, -0.9, eps=0.01, r=0.3)  # xi > eta
+    with pytest.raises(pfe.PfeError):
+        pfe.pfe_design_filter("pq", -0.9, -0.8, eps=0.01, r=1.5)  # r outside (0, 1)
+    with pytest.raises(pfe.PfeError):
+        pfe.pfe_design_filter("dirac", -0.9, -0.8, phi=0.0)
