@@ -287,7 +287,7 @@ pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeff
  * selects PFE_P_METHOD = 1 the samples' block Lanczos solves run whole, concurrently from those
  * threads, each on its own stream; each sample releases its work buffers when its solve ends (its
  * eigenvectors stay), and a sample that ran out of device memory beside the others is solved again
- * afterwards, alone.
+ * afterwards, alone.  All contexts of a batch select the same method (PFE_E_ARG otherwise).
  * In the stats of every sample seconds_filter is the batch's shared filter time.
  * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);

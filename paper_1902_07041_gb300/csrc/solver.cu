@@ -1576,8 +1576,12 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
   if (cudaSetDevice(c0->device) != cudaSuccess) return pfe_fail(c0, PFE_E_CUDA, "cudaSetDevice failed");
   std::vector<pfe_status> status(nsamples, PFE_OK);
   const int32_t nthreads = c0->p_batch_threads;
-  bool all_bks = true;
-  for (int32_t i = 0; i < nsamples; ++i) all_bks = all_bks && ctxs[i]->p_method == 1;
+  bool all_bks = true, any_bks = false;
+  for (int32_t i = 0; i < nsamples; ++i) {
+    all_bks = all_bks && ctxs[i]->p_method == 1;
+    any_bks = any_bks || ctxs[i]->p_method == 1;
+  }
+  if (any_bks && !all_bks) return pfe_fail(c0, PFE_E_ARG, "batch contexts must all select the same PFE_P_METHOD");
   if (all_bks) {
     // block Lanczos samples: every sample's solve on its own stream, the samples concurrently from
     // the host threads (their kernels overlap on the device); no shared graph
