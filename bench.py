@@ -1,21 +1,30 @@
 #!/usr/bin/env python
 """Benchmark: time to all interval eigenpairs (residual <= 1e-8) of a synthetic glass Hessian,
-with the filter's SpMM throughput and the mixed-precision form beside the FP64 form.
+with the filter's throughput against its roofline and the mixed-precision form beside the FP64 form.
 
-One step = one full solve through the C ABI: lambda_max bound, filter design, count estimate and
-the filtered subspace iteration (filter, CholQR2, Rayleigh-Ritz, residuals, locking) until every
-eigenpair in the interval has converged.  Inputs are seeded and synthetic (glassgen).
+One step = one outer iteration of the filtered subspace iteration (Alg. 4: the filter p_m(Ht) on
+the active block, CholQR2 against the locked vectors, Rayleigh-Ritz with H, residuals, locking),
+through the stepwise C ABI (pfe_solve_begin / pfe_solve_iterate / pfe_solve_end).  A solve's set-up
+(context creation, lambda_max bound, filter design, count estimate, start block) belongs to its
+first step and its results to its last; when a solve ends, the next step starts a new one.  Exactly
+--steps steps are timed.  `value` is the time to all interval eigenpairs of the solves completed in
+the timed region (when none completes there, the solve in flight is run to its end and timed whole).
+Inputs are seeded and synthetic (glassgen).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl native|reference]
 
 Under torchrun (N > 1) every rank solves its own replica (the single solve does not shard: replicas
-only); the value is the max over ranks of the per-step time.  --impl reference times the FP64 CPU
-oracle on a bounded sample of the same workload and extrapolates to the solve's work.
+only); times are the max over ranks.  --impl reference times the FP64 CPU oracle on a bounded sample
+of the same workload: each step applies the oracle's Alg. 2 filter of the workload's degree to one
+column per host core, and the time to all eigenpairs is extrapolated from the measured rates to the
+subspace iteration's work on this workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -30,26 +39,34 @@ METRIC = "time to all interval eigenpairs (resid≤1e-8); filter SpMM GB/s; mixe
 # Workloads (binary glass of glassgen: density 0.06/A^3, RSA d_min 2.2 A, bonds r < 3.5 A,
 # k lognormal(1, 0.3), 64 % A / 36 % B).  The N = 100,000 interval keeps the lower edge
 # 0.02 lambda_max of the stated configuration and ends where it holds ~700 modes (598 found):
-# the literal upper edge 0.03 lambda_max holds ~4,980 modes for this generator.
+# the literal upper edge 0.03 lambda_max holds ~4,990 modes for this generator.
 WORKLOADS = {
     "glass-n100k-fp64": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=0),
     "glass-n100k-mixed": dict(N=100_000, seed=1, lo=0.02, hi=0.0214, precision=1),
     "glass-n1k-fp64": dict(N=1_000, seed=0, lo=0.02, hi=0.05, precision=0),
     "glass-n20k-fp64": dict(N=20_000, seed=1, lo=0.02, hi=0.0214, precision=0),
-    # the literal N = 100,000 interval [0.02, 0.03] lambda_max (~4,980 modes): spectrum slicing into
-    # slices of ~700 modes, each solved by block Lanczos
-    "glass-n100k-literal-sliced": dict(N=100_000, seed=1, lo=0.02, hi=0.03, precision=0, method=1, sliced=700),
 }
 DEFAULT = "glass-n100k-fp64"
 
-FP64_PEAK_TFLOPS = 152 * 2.070e9 * 2 * 2 / 1e12  # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
-# DRAM traffic / algorithmic bytes of the fused step, from ncu captures per form and type
-# (N = 100,000; k = 64 FP64, k = 128 FP32; profiles/filter_step_f64_n100k.md, filter_step_f32_n100k.md,
-# filter_step_r1_f64_n100k.md, filter_step_r1_f32_n100k.md; the rank-1 figures are the mean of a
-# STEP and a STEP_ACC launch, which the filter alternates)
-TRAFFIC_RATIO = {("bsr", 8): 872.490752 / 854.171476, ("bsr", 4): 830.966784 / 813.542884,
-                 ("rank1", 8): 663.502336 / 648.400020, ("rank1", 4): 645.863808 / 633.657156}
+# Work of the subspace iteration on a workload, as its GPU solve counted it (the same method with the
+# same width, degree and locking does the same work on any machine): outer iterations, products with
+# H (the filter's m per active column and iteration plus the Rayleigh-Ritz products), and the active
+# and locked column counts of each iteration.  The reference arm scales the oracle's measured rates
+# by these counts; the native arm prints its own counts beside them.
+SOLVE_WORK = {
+    "glass-n100k-fp64": dict(width=994, degree=417, iterations=13, matvecs=4_178_687, active=None, locked=None),
+}
+
+# DRAM traffic per launch of the dominant kernel, measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on one GB300 for the launch shape the solve runs, keyed by the kernel's
+# source file hash: a changed kernel invalidates the number.  (kernel, columns, FP bytes) -> bytes.
+TRAFFIC = {}
 R1_SHAPES = (7, 8, 9)  # kernel shapes of the fused step that run on the rank-1 form
+
+
+def _src_hash(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def peaks():
@@ -133,75 +150,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------------------------
-def make_problem(wl):
-    import glassgen
-    import paper_1902_07041_gb300 as pfe
-
-    g = glassgen.generate(wl["N"], wl["seed"])
-    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
-    return g, rp, ci, vals
-
-
-def one_step(pfe, torch, g, rp, ci, vals, wl, ev):
-    """create (H2D) -> [estimate + solve] -> eigenpairs to host (D2H) -> destroy.
-    ev = (e_start, e_solve0, e_solve1, e_end) CUDA events on the default stream."""
-    ev[0].record()
-    ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
-    try:
-        pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, wl["precision"])
-        pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, wl.get("method", 0))
-        if wl.get("sliced"):
-            pfe.pfe_set_param(ctx, pfe.PFE_P_SLICE_TARGET, wl["sliced"])
-        torch.cuda.synchronize()
-        ev[1].record()
-        lmax, _ = pfe.pfe_estimate(ctx)
-        pfe.pfe_set_interval(ctx, wl["lo"] * lmax, wl["hi"] * lmax)
-        nf, _ = pfe.pfe_solve_sliced(ctx) if wl.get("sliced") else pfe.pfe_solve(ctx)
-        ev[2].record()
-        lam, vecs, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
-        stats = pfe.pfe_get_stats(ctx)
-    finally:
-        pfe.pfe_destroy(ctx)
-    ev[3].record()
-    torch.cuda.synchronize()
-    stats["h2d_bytes"] = rp.nbytes + ci.nbytes + vals.nbytes + g.mass.nbytes
-    stats["d2h_bytes"] = lam.nbytes + vecs.nbytes + res.nbytes
-    stats["max_rel_residual"] = float(res.max() / lmax) if nf else 0.0
-    stats["n_found"] = nf
-    return stats
-
-
-def oracle_sample(g, stats, budget_s=20.0):
-    """Oracle (FP64 CPU, single thread) on a bounded sample of the same workload: seconds per
-    single-vector Chebyshev product on this H and seconds per dense flop (Householder QR of an
-    n x 32 block), extrapolated to the solve's MatVec count and dense flop count."""
-    import numpy as np
-
-    import oracle
-
-    H = oracle.csr_from_springs(g)
-    n = H.n
-    X = oracle.normal_block(7, 0, n, 2)
-    m = 4
-    t0 = time.perf_counter()
-    oracle.cheb_filter(H, 0.5, 0.5, np.ones(m + 1) / (m + 1), X)
-    t_mv = (time.perf_counter() - t0) / (2 * m)
-    k = 32
-    Xq = oracle.normal_block(8, 0, n, k)
-    t0 = time.perf_counter()
-    oracle.householder_qr(Xq)
-    t_qr = time.perf_counter() - t0
-    sec_per_flop = t_qr / (4.0 * n * k * k)
-    width = stats["width"]
-    dense_flops = stats["iterations"] * 12.0 * n * width * width  # QR + RR + projections, per iteration
-    est = stats["matvecs"] * t_mv + dense_flops * sec_per_flop
-    sample = (f"oracle Alg. 2 on {2 * m} single-vector products of this H ({t_mv * 1e3:.1f} ms each) and a "
-              f"Householder QR of {n}x{k} ({t_qr:.2f} s), extrapolated to the GPU solve's "
-              f"{stats['matvecs']} MatVecs and ~{dense_flops:.3g} dense flops")
-    return est, sample
-
-
 def max_over_ranks(values, dist, device):
     """Max over the ranks of each timing: replicas run concurrently, so the job takes as long as its
     slowest rank. dist None (one process) returns the values unchanged."""
@@ -214,49 +162,299 @@ def max_over_ranks(values, dist, device):
     return [float(x) for x in t.cpu()]
 
 
+# ============================================================================================
+# The oracle on the host cores (reference arm and cpu_baseline).  Only the oracle and the input
+# generator are loaded here: no part of the GPU library.
+# ============================================================================================
+_W = {}
+
+
+def _worker_init(wl):
+    import glassgen
+    import oracle
+
+    g = glassgen.generate(wl["N"], wl["seed"])
+    _W["H"] = oracle.csr_from_springs(g)
+
+
+def _worker_filter(args):
+    """The oracle's Alg. 2 on one seeded column of this worker's copy of H; returns seconds."""
+    import oracle
+
+    c, d, coef, col = args
+    H = _W["H"]
+    x = oracle.normal_block(17, 1, H.n, 1, col)
+    t0 = time.perf_counter()
+    oracle.cheb_filter(H, c, d, coef, x)
+    return time.perf_counter() - t0
+
+
+def _worker_count(args):
+    """The oracle's count estimate (Sec. 2.4) with its own share of the probe vectors."""
+    import oracle
+
+    c, d, xi, eta, m_vec, seed = args
+    return oracle.count_estimate(_W["H"], c, d, xi, eta, 100, "none", m_vec, seed)
+
+
+class OracleSample:
+    """The FP64 CPU oracle on a bounded sample of a workload, on `cores` host processes.
+
+    Set-up: H, the Lanczos bound, the filter degree (eq. (thresh), r = sqrt(0.1), no damping) and the
+    width rule of the solver (max(1.5 x the count estimate of [a, b], 1.1 x the estimate of the margin
+    window + 8), M = 30 probe vectors shared over the processes), and the oracle's dense rate from one
+    Householder QR of an n x 32 block.  step(): the oracle's Alg. 2 at the workload's degree on one
+    column per process, in parallel.  estimate(): the time to all eigenpairs from those rates and the
+    subspace iteration's work on this workload."""
+
+    def __init__(self, wl, cores=None):
+        import numpy as np
+
+        import glassgen
+        import oracle
+
+        self.wl = wl
+        self.cores = int(cores or os.cpu_count() or 1)
+        g = glassgen.generate(wl["N"], wl["seed"])
+        self.H = H = oracle.csr_from_springs(g)
+        self.n = H.n
+        _, _, lmax = oracle.lanczos_lmax(H, 30, 0)
+        self.lmax = lmax
+        self.c = self.d = 0.5 * lmax
+        self.xi = (wl["lo"] * lmax - self.c) / self.d
+        self.eta = (wl["hi"] * lmax - self.c) / self.d
+        self.eps = 0.25 * (self.eta - self.xi)
+        self.degree = oracle.select_degree(self.xi, self.eta, self.eps, 0.1 ** 0.5, "none")
+        self.coef = oracle.filter_coeffs(self.xi, self.eta, self.eps, self.degree, "none")
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.cores, initializer=_worker_init, initargs=(wl,))
+        t0 = time.perf_counter()
+        per = max(1, -(-30 // self.cores))
+        jobs = [(self.c, self.d, self.xi, self.eta, per, s) for s in range(-(-30 // per))]
+        wjobs = [(self.c, self.d, self.xi - self.eps, self.eta + self.eps, per, s) for s in range(-(-30 // per))]
+        cnt = self.pool.map(_worker_count, jobs + wjobs)
+        self.count = float(np.mean(cnt[:len(jobs)]))
+        self.window = float(np.mean(cnt[len(jobs):]))
+        self.width = int(np.ceil(max(1.5 * self.count, 1.1 * self.window + 8, 16)))
+        self.setup_count_s = time.perf_counter() - t0
+        k = 32
+        Xq = oracle.normal_block(8, 0, self.n, k)
+        t0 = time.perf_counter()
+        oracle.householder_qr(Xq)
+        self.qr_s = time.perf_counter() - t0
+        self.sec_per_dense_flop = self.qr_s / (4.0 * self.n * k * k)
+        self.step_times = []
+        self._col = 0
+
+    def step(self):
+        """One step: the filter on one column per process; returns the step's wall seconds."""
+        args = [(self.c, self.d, self.coef, self._col + i) for i in range(self.cores)]
+        self._col += self.cores
+        t0 = time.perf_counter()
+        self.pool.map(_worker_filter, args, chunksize=1)
+        t = time.perf_counter() - t0
+        self.step_times.append(t)
+        return t
+
+    def sec_per_matvec(self):
+        """Wall seconds per single-vector product with H with every process busy (median step)."""
+        return statistics.median(self.step_times) / (self.cores * self.degree)
+
+    def estimate(self, work):
+        """Time to all eigenpairs of the subspace iteration with `work` (iterations, MatVecs, and the
+        active and locked columns per iteration when known): products with H at the parallel rate,
+        the dense steps of the oracle's iteration (two Gram-Schmidt passes against the locked block,
+        Householder QR, the Gram matrix, X Q and W Q: 8 n a l + 10 n a^2 flops for a active and l
+        locked columns, plus about 20 a^3 for the Jacobi eigensolver) at its single-thread rate."""
+        n = self.n
+        it = work["iterations"]
+        act = work.get("active")
+        lck = work.get("locked")
+        if not act:
+            a = work["matvecs"] / (it * (work["degree"] + 2))  # mean active width
+            act = [a] * it
+            lck = [0.5 * (work["width"] - a)] * it
+        dense = sum(8.0 * n * a * l + 10.0 * n * a * a + 20.0 * a ** 3 for a, l in zip(act, lck))
+        t_mv = work["matvecs"] * self.sec_per_matvec()
+        t_dense = dense * self.sec_per_dense_flop
+        return t_mv + t_dense, t_mv, t_dense, dense
+
+    def describe(self):
+        return (f"oracle Alg. 2 (degree {self.degree}) on one seeded column per process, {self.cores} processes "
+                f"in parallel on N = {self.wl['N']} (median {statistics.median(self.step_times):.2f} s a step, "
+                f"{1e3 * self.sec_per_matvec():.3f} ms per product with H per process); dense rate from a "
+                f"Householder QR of {self.n} x 32 ({self.qr_s:.2f} s, one core)")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_full_solve_n1000():
+    """The oracle's complete subspace iteration on the N = 1,000 glass (seed 0, [0.02, 0.05] lambda_max,
+    degree 40, width 256), single-threaded: a full solve, not a sample."""
+    import oracle
+    import glassgen
+
+    g = glassgen.generate(1000, 0)
+    H = oracle.csr_from_springs(g)
+    t0 = time.perf_counter()
+    _, _, lmax = oracle.lanczos_lmax(H, 30, 0)
+    c = d = 0.5 * lmax
+    a, b = 0.02 * lmax, 0.05 * lmax
+    xi, eta = (a - c) / d, (b - c) / d
+    coef = oracle.filter_coeffs(xi, eta, 0.25 * (eta - xi), 40, "none")
+    r = oracle.si_solve(H, a, b, 0.0, lmax, coef, 256, oracle.normal_block(0, 0, H.n, 256), max_iter=200)
+    return {"seconds": time.perf_counter() - t0, "n_found": int(r.lam.size), "iterations": r.iters,
+            "matvecs": r.matvecs, "status": r.status, "cores": 1}
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-
-    g, rp, ci, vals = make_problem(wl)
-    # the solve's work: MatVecs and width of the GPU form are not known here; use the oracle's own
-    # filter design for the same interval and the paper's iteration model (n_iter from stats file
-    # if present, else 13 iterations at width 1.6 x the count estimate).
-    import oracle
-
-    H = oracle.csr_from_springs(g)
-    th, rb, lmax = oracle.lanczos_lmax(H, 30, 0)
-    c = d = 0.5 * lmax
-    xi, eta = (wl["lo"] * lmax - c) / d, (wl["hi"] * lmax - c) / d
-    eps = 0.25 * (eta - xi)
-    m = oracle.select_degree(xi, eta, eps, 0.1 ** 0.5, "none")
-    cnt = oracle.count_estimate(H, c, d, xi, eta, 100, "none", 4, 0)  # 4 probe vectors keep it bounded
-    width = int(max(1.5 * cnt, 16))
-    iters = 13
-    stats = {"width": width, "iterations": iters, "matvecs": int(iters * 0.75 * width * m)}
-    times = []
-    est = sample = None
-    for _ in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        est, sample = oracle_sample(g, stats)
-        times.append(time.perf_counter() - t0)
+    work = SOLVE_WORK.get(args.workload)
+    t_setup = time.perf_counter()
+    smp = OracleSample(wl)
+    setup_s = time.perf_counter() - t_setup
+    for _ in range(args.warmup):
+        smp.step()
+    smp.step_times.clear()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        smp.step()
+    timed = time.perf_counter() - t0
+    smp.close()
+    if work is None:
+        work = dict(width=smp.width, degree=smp.degree, iterations=13,
+                    matvecs=int(13 * smp.width * (smp.degree + 2) * 0.75))
+    est, t_mv, t_dense, dense = smp.estimate(work)
+    full = oracle_full_solve_n1000()
+    sample = (smp.describe() + f"; extrapolated to the subspace iteration's work on this workload "
+              f"({work['iterations']} iterations, {work['matvecs']} products with H, ~{dense:.3g} dense flops): "
+              f"{t_mv:.0f} s of products, {t_dense:.0f} s of dense steps")
     line = {"metric": METRIC, "value": est, "unit": "s", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * est,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * timed / max(args.steps, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, **wl, "degree": m, "width": width},
-            "cpu_baseline": {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": sample + f"; {iters} iterations at width {width}, degree {m} assumed"},
+            "data": "synthetic",
+            "config": {"workload": args.workload, **wl, "degree": smp.degree, "width": smp.width,
+                       "count_estimate": smp.count, "window_estimate": smp.window,
+                       "step": f"the oracle's Alg. 2 at degree {smp.degree} on {smp.cores} columns, one per "
+                               f"host process"},
+            "cpu_baseline": {"value": est, "unit": "s", "cores": smp.cores, "kind": "oracle", "sample": sample,
+                             "extrapolated": True, "oracle_full_solve_n1000": full},
             "e2e": {"value": est, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": times[-1]}
+            "timed_wall_s": timed, "setup_s": setup_s}
     print(json.dumps(line), flush=True)
+
+
+# ============================================================================================
+# Native arm: the GPU library through its C ABI
+# ============================================================================================
+class SteppedSolve:
+    """One subspace-iteration solve driven a step at a time through the stepwise C ABI.
+
+    host=False: the context is created from device-resident BSR arrays (inputs in HBM) and the
+    eigenvectors are exported to a device buffer.  host=True: created from pinned host arrays
+    (H2D inside) and the eigenpairs copied to pinned host buffers (D2H inside)."""
+
+    def __init__(self, pfe, torch, arrays, wl, host):
+        self.pfe, self.torch, self.arrays, self.wl, self.host = pfe, torch, arrays, wl, host
+        self.ctx = None
+        self.done = False
+        self.profile = []  # (active, locked) before each iteration
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev1 = torch.cuda.Event(enable_timing=True)
+
+    def start(self):
+        pfe, a = self.pfe, self.arrays
+        self.ev0.record()
+        if self.host:
+            self.ctx = pfe.pfe_create(a["N"], a["rp_h"], a["ci_h"], a["vals_h"], a["mass_h"])
+        else:
+            self.ctx = pfe.pfe_create(a["N"], a["rp_d"], a["ci_d"], a["vals_d"], a["mass_d"],
+                                      flags=pfe.PFE_DEVICE_PTRS)
+        pfe.pfe_set_param(self.ctx, pfe.PFE_P_PRECISION, self.wl["precision"])
+        pfe.pfe_set_param(self.ctx, pfe.PFE_P_METHOD, 0)
+        lmax, _ = pfe.pfe_estimate(self.ctx)
+        self.lmax = lmax
+        pfe.pfe_set_interval(self.ctx, self.wl["lo"] * lmax, self.wl["hi"] * lmax)
+        pfe.pfe_solve_begin(self.ctx)
+
+    def iterate(self):
+        st = self.pfe.pfe_get_stats(self.ctx)
+        self.profile.append((st["active"], st["locked"]))
+        self.done = self.pfe.pfe_solve_iterate(self.ctx)
+        return self.done
+
+    def finish(self):
+        pfe, torch = self.pfe, self.torch
+        nf, st = pfe.pfe_solve_end(self.ctx)
+        n = 3 * self.arrays["N"]
+        if self.host:
+            self.vecs = torch.empty((max(nf, 1), n), dtype=torch.float64).pin_memory()
+            lam, _, res = pfe.pfe_get_eigenpairs(self.ctx, n, nf, vecs_out=self.vecs)
+        else:
+            self.vecs = torch.empty((max(nf, 1), n), dtype=torch.float64, device="cuda")
+            lam, _, res = pfe.pfe_get_eigenpairs(self.ctx, n, nf, vecs_out=self.vecs)
+        self.stats = pfe.pfe_get_stats(self.ctx)
+        pfe.pfe_destroy(self.ctx)
+        self.ctx = None
+        self.ev1.record()
+        self.lam, self.res, self.n_found = lam, res, nf
+        self.max_rel_residual = float(res.max() / self.lmax) if nf else 0.0
+
+    def abandon(self):
+        if self.ctx is not None:
+            self.pfe.pfe_solve_end(self.ctx, raise_on_error=False)
+            self.pfe.pfe_destroy(self.ctx)
+            self.ctx = None
+
+    def seconds(self):
+        return self.ev0.elapsed_time(self.ev1) / 1e3
+
+
+def whole_solve(pfe, torch, arrays, wl, host=False, method=0):
+    """One complete solve through pfe_solve (the call a user makes), timed by CUDA events."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 3 * arrays["N"]
+    e0.record()
+    if host:
+        ctx = pfe.pfe_create(arrays["N"], arrays["rp_h"], arrays["ci_h"], arrays["vals_h"], arrays["mass_h"])
+    else:
+        ctx = pfe.pfe_create(arrays["N"], arrays["rp_d"], arrays["ci_d"], arrays["vals_d"], arrays["mass_d"],
+                             flags=pfe.PFE_DEVICE_PTRS)
+    try:
+        pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, wl["precision"])
+        pfe.pfe_set_param(ctx, pfe.PFE_P_METHOD, method)
+        lmax, _ = pfe.pfe_estimate(ctx)
+        pfe.pfe_set_interval(ctx, wl["lo"] * lmax, wl["hi"] * lmax)
+        nf, _ = pfe.pfe_solve(ctx)
+        if host:
+            vecs = torch.empty((max(nf, 1), n), dtype=torch.float64).pin_memory()
+        else:
+            vecs = torch.empty((max(nf, 1), n), dtype=torch.float64, device="cuda")
+        lam, _, res = pfe.pfe_get_eigenpairs(ctx, n, nf, vecs_out=vecs)
+        stats = pfe.pfe_get_stats(ctx)
+    finally:
+        pfe.pfe_destroy(ctx)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"seconds": e0.elapsed_time(e1) / 1e3, "lam": lam, "res": res, "vecs": vecs, "n_found": nf,
+            "lmax": lmax, "stats": stats, "max_rel_residual": float(res.max() / lmax) if nf else 0.0}
+
+
+def fp64_peak(pfe, torch):
+    """FP64 FMA throughput of this GPU, measured now (best of three timings of 5 launches)."""
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    return max(pfe.pfe_probe_fp64_fma(4000, 5, sink) for _ in range(3))
 
 
 def run_native(args, wl):
     import numpy as np
     import torch
 
+    import glassgen
     import paper_1902_07041_gb300 as pfe
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,108 +467,180 @@ def run_native(args, wl):
 
         dist.init_process_group("nccl")
     pfe.load()
-    g, rp, ci, vals = make_problem(wl)
+    g = glassgen.generate(wl["N"], wl["seed"])
+    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    arrays = {"N": g.n_atoms, "rp_h": pin(rp), "ci_h": pin(ci), "vals_h": pin(vals), "mass_h": pin(g.mass)}
+    for key in ("rp", "ci", "vals", "mass"):
+        arrays[key + "_d"] = arrays[key + "_h"].cuda()
+    h2d_bytes = sum(arrays[k + "_h"].numel() * arrays[k + "_h"].element_size() for k in ("rp", "ci", "vals", "mass"))
+    torch.cuda.synchronize()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    evs = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(4)]  # noqa: E731
+    # ---- warm-up: W steps of a solve that is then dropped (kernel-shape tuning, library handles)
+    cur = SteppedSolve(pfe, torch, arrays, wl, host=False)
+    cur.start()
     for _ in range(args.warmup):
-        one_step(pfe, torch, g, rp, ci, vals, wl, evs())
+        if cur.iterate():
+            cur.finish()
+            cur = SteppedSolve(pfe, torch, arrays, wl, host=False)
+            cur.start()
+    cur.abandon()
+    cur = None
+    # ---- timed region: exactly K steps
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
-    steps = []
-    t0 = time.perf_counter()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    t_start.record()
+    completed = []
     for _ in range(args.steps):
-        e = evs()
-        st = one_step(pfe, torch, g, rp, ci, vals, wl, e)
-        st["solve_s"] = e[1].elapsed_time(e[2]) / 1e3
-        st["e2e_s"] = e[0].elapsed_time(e[3]) / 1e3
-        steps.append(st)
+        if cur is None:
+            cur = SteppedSolve(pfe, torch, arrays, wl, host=False)
+            cur.start()
+        if cur.iterate():
+            cur.finish()
+            completed.append(cur)
+            cur = None
+    t_end.record()
     barrier()
-    wall = time.perf_counter() - t0
+    wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    solve_s = sum(s["solve_s"] for s in steps) / len(steps)
-    e2e_s = sum(s["e2e_s"] for s in steps) / len(steps)
-    solve_s, e2e_s = max_over_ranks([solve_s, e2e_s], dist, "cuda")
-    last = steps[-1]
-    # roofline of the dominant kernel (the fused filter step): FP64 is bound by the FP64 pipe
+    timed_s = t_start.elapsed_time(t_end) / 1e3
+    # launches of this library's kernels inside the timed region: each solve there created its context
+    # there, and one context works at a time, so its process-wide launch count since creation is exact
+    gpu_launches = sum(int(s.stats["kernel_launches"]) for s in completed)
+    if cur is not None:
+        gpu_launches += int(pfe.pfe_get_stats(cur.ctx)["kernel_launches"])
+    if not completed:  # the timed steps did not finish a solve: run the one in flight to its end
+        while not cur.iterate():
+            pass
+        cur.finish()
+        torch.cuda.synchronize()
+        completed.append(cur)
+        cur = None
+    if cur is not None:
+        cur.abandon()
+    torch.cuda.synchronize()
+    solve_s = statistics.mean(s.seconds() for s in completed)
+    solve_s, timed_s = max_over_ranks([solve_s, timed_s], dist, "cuda")
+    first = completed[0]
+    st = first.stats
     nnzb = int(ci.size)
     hbm, hbm_src = peaks()
-    if last["filter_col_steps"] > 0:
-        r1 = last["filter_shape_f64"] in R1_SHAPES
-        form = "rank1" if r1 else "bsr"
-        secs64 = last["seconds_filter"] - last["seconds_filter_f32"]
-        _, fl = filter_work(g.n_atoms, nnzb, 1, 8, 8, r1)
-        flops = fl * last["filter_col_steps"]
-        achieved = flops / secs64 / 1e12
-        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 8, 8, r1)
-        avg_k = last["filter_col_steps"] / max(last["filter_launches"], 1)
-        bl, _ = filter_work(g.n_atoms, nnzb, int(round(avg_k)), 8, 8, r1)
-        ratio = TRAFFIC_RATIO.get((form, 8))
-        roof = {"bound": "alu", "kernel": ("k_r1_step<double>" if r1 else "k_bsr_step<double>") +
-                " (fused Chebyshev step, shape %d)" % last["filter_shape_f64"], "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": ratio * bl if ratio else None,
-                "traffic_note": ("bytes per average launch: algorithmic x the ncu-measured DRAM/algorithmic "
-                                 "ratio of the k = 64 captures") if ratio else "no ncu capture of this kernel yet",
-                "peak_source": "152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
-                "filter_gbs_fp64": (b1 / last["width"]) * last["filter_col_steps"] / secs64 / 1e9,
-                "launches": last["filter_launches"], "operator_form": form}
-    else:
-        r1 = last["filter_shape_f32"] in R1_SHAPES
-        secs32 = last["seconds_filter_f32"]
-        b1, _ = filter_work(g.n_atoms, nnzb, last["width"], 4, 4, r1)
-        gbs = (b1 / last["width"]) * last["filter_col_steps_f32"] / secs32 / 1e9
-        roof = {"bound": "hbm", "kernel": "k_r1_step<float>" if r1 else "k_bsr_step<float>", "achieved": gbs,
-                "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "peak_source": hbm_src}
+
+    # ---- roofline of the dominant kernel: the fused filter step, FP64, bound by the FP64 pipe
+    peak64 = fp64_peak(pfe, torch)
+    r1 = st["filter_shape_f64"] in R1_SHAPES
+    secs64 = st["seconds_filter"] - st["seconds_filter_f32"]
+    _, fl1 = filter_work(g.n_atoms, nnzb, 1, 8, 8, r1)
+    achieved = fl1 * st["filter_col_steps"] / secs64 / 1e12
+    avg_k = st["filter_col_steps"] / max(st["filter_launches"], 1)
+    b_avg, _ = filter_work(g.n_atoms, nnzb, int(round(avg_k)), 8, 8, r1)
+    kname = "k_r1_step<double>" if r1 else "k_bsr_step<double>"
+    tr = TRAFFIC.get((kname, 8))
+    traffic = None
+    if tr and tr["src"] == _src_hash(tr["file"]):
+        traffic = tr["bytes"] * b_avg / tr["alg_bytes"]  # scaled from the captured launch to the average one
+    roof = {"bound": "alu", "kernel": kname + " (fused Chebyshev step, shape %d)" % st["filter_shape_f64"],
+            "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
+            "traffic": traffic, "algorithmic_bytes_per_launch": b_avg, "avg_columns_per_launch": avg_k,
+            "peak_source": "FP64 FMA throughput measured in this run (pfe_probe_fp64_fma: 8 independent chains "
+                           "per thread, 8 CTAs of 256 threads per SM)",
+            "achieved_how": "the rank-1 form's flops (12 per off-diagonal block and column, 18 per diagonal block "
+                            "and column, 6 per vector element) x column-steps / CUDA-event seconds of the FP64 "
+                            "filter sweeps on the launching stream",
+            "filter_gbs_fp64": b_avg * st["filter_launches"] / secs64 / 1e9, "hbm_peak_gbs": hbm,
+            "launches": st["filter_launches"], "operator_form": "rank1" if r1 else "bsr"}
+    work_live = {"width": st["width"], "degree": st["degree"], "iterations": st["iterations"],
+                 "matvecs": st["matvecs"], "active": [a for a, _ in first.profile],
+                 "locked": [lk for _, lk in first.profile]}
     line = {
         "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * solve_s, "higher_is_better": False,
+        "warmup": args.warmup, "ms_per_step": 1e3 * timed_s / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["precision"] == 0 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, **wl, "n": 3 * wl["N"], "nnzb": nnzb, "width": last["width"],
-                   "degree": last["degree"], "iterations": last["iterations"], "n_found": last["n_found"],
-                   "matvecs": last["matvecs"], "parallelism": f"replicas x{world}",
-                   "l2": "working set (multivectors of n x width) far above the 129 MB L2"},
+        "config": {"workload": args.workload, **wl, "n": 3 * wl["N"], "nnzb": nnzb, "width": st["width"],
+                   "degree": st["degree"], "iterations": st["iterations"], "n_found": first.n_found,
+                   "matvecs": st["matvecs"], "parallelism": f"replicas x{world}",
+                   "step": "one outer iteration of the subspace iteration (a solve's set-up in its first step)",
+                   "solves_completed_in_timed_region": len(completed),
+                   "l2": "no flush: every step streams multivectors of n x width FP64 (2.4 GB each) through the "
+                         "129 MB L2"},
         "roofline": roof,
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(last["h2d_bytes"]),
-                "d2h_bytes_per_step": int(last["d2h_bytes"])},
-        "gpu_launches": int(sum(s["kernel_launches"] for s in steps)),
+        "gpu_launches": gpu_launches,
         "clocks": clocks,
-        "breakdown_s": {"filter": last["seconds_filter"], "orth": last["seconds_orth"], "rr": last["seconds_rr"]},
-        "max_rel_residual": last["max_rel_residual"], "wall_s": wall,
+        "breakdown_s": {"filter": st["seconds_filter"], "orth": st["seconds_orth"], "rr": st["seconds_rr"]},
+        "max_rel_residual": first.max_rel_residual, "wall_s": wall, "timed_s": timed_s,
+        "work": work_live,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample = oracle_sample(g, last)
-        line["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample}
-    plain_si = wl["precision"] == 0 and wl.get("method", 0) == 0 and not wl.get("sliced")
+
+    # ---- end to end through the public API: pinned host BSR in, host eigenpairs out
+    e2e = whole_solve(pfe, torch, arrays, wl, host=True)
+    line["e2e"] = {"value": e2e["seconds"], "unit": "s", "h2d_bytes_per_step": int(h2d_bytes),
+                   "d2h_bytes_per_step": int(e2e["lam"].nbytes + e2e["res"].nbytes +
+                                             e2e["n_found"] * 3 * wl["N"] * 8),
+                   "step": "one complete solve: pfe_create from pinned host arrays, pfe_estimate, pfe_solve, "
+                           "pfe_get_eigenpairs into pinned host buffers, pfe_destroy",
+                   "n_found": e2e["n_found"], "max_rel_residual": e2e["max_rel_residual"]}
+    plain_si = wl["precision"] == 0
     if rank == 0 and args.mixed and plain_si:
-        wm = dict(wl, precision=1)  # the FP64 warm-up steps above also warmed this path's set-up
-        e = evs()
-        sm = one_step(pfe, torch, g, rp, ci, vals, wm, e)
-        b1, _ = filter_work(g.n_atoms, nnzb, sm["width"], 4, 4, sm["filter_shape_f32"] in R1_SHAPES)
-        gbs32 = (b1 / sm["width"]) * sm["filter_col_steps_f32"] / max(sm["seconds_filter_f32"], 1e-12) / 1e9
-        line["mixed"] = {"value": e[1].elapsed_time(e[2]) / 1e3, "unit": "s", "fp64_sweeps": sm["fp64_sweeps"],
-                         "iterations": sm["iterations"], "n_found": sm["n_found"],
-                         "max_rel_residual": sm["max_rel_residual"],
+        wm = dict(wl, precision=1)
+        sm = whole_solve(pfe, torch, arrays, wm)
+        s2 = sm["stats"]
+        b1, _ = filter_work(g.n_atoms, nnzb, s2["width"], 4, 4, s2["filter_shape_f32"] in R1_SHAPES)
+        gbs32 = (b1 / s2["width"]) * s2["filter_col_steps_f32"] / max(s2["seconds_filter_f32"], 1e-12) / 1e9
+        # per-eigenpair agreement of the mixed form with the FP64 form (e2e solve) on the same matrix
+        agree = {}
+        if sm["n_found"] == e2e["n_found"] and sm["n_found"] > 0:
+            lam64, lam32 = e2e["lam"], sm["lam"]
+            rel = np.abs(lam32 - lam64) / np.abs(lam64)
+            V64 = e2e["vecs"][:e2e["n_found"]].cuda()
+            V32 = sm["vecs"][:sm["n_found"]]
+            # largest principal angle between the two computed spaces: ||V32 - V64 (V64^T V32)||_2
+            P = V64 @ V32.T
+            Dv = V32 - P.T @ V64
+            sin_max = float(torch.linalg.eigvalsh(Dv @ Dv.T).max().clamp(min=0).sqrt())
+            agree = {"max_eig_rel_diff": float(rel.max()), "median_eig_rel_diff": float(np.median(rel)),
+                     "subspace_sin_max": sin_max}
+            del V64, P, Dv
+        line["mixed"] = {"value": sm["seconds"], "unit": "s", "fp64_sweeps": s2["fp64_sweeps"],
+                         "iterations": s2["iterations"], "n_found": sm["n_found"],
+                         "max_rel_residual": sm["max_rel_residual"], "vs_fp64_form": agree,
                          "filter_f32": {"achieved": gbs32, "peak": hbm, "unit": "GB/s", "frac": gbs32 / hbm,
-                                        "peak_source": hbm_src, "shape": sm["filter_shape_f32"]}}
+                                        "peak_source": hbm_src, "shape": s2["filter_shape_f32"]},
+                         "breakdown_s": {"filter": s2["seconds_filter"], "filter_f32": s2["seconds_filter_f32"],
+                                         "orth": s2["seconds_orth"], "rr": s2["seconds_rr"]}}
     if rank == 0 and args.block_lanczos and plain_si:
-        wb = dict(wl, method=1)
-        e = evs()
-        sb = one_step(pfe, torch, g, rp, ci, vals, wb, e)
-        line["block_lanczos"] = {"value": e[1].elapsed_time(e[2]) / 1e3, "unit": "s", "n_found": sb["n_found"],
-                                 "matvecs": sb["matvecs"], "restarts": sb["restarts"], "basis": sb["basis"],
-                                 "block": sb["width"], "max_rel_residual": sb["max_rel_residual"],
-                                 "breakdown_s": {"filter": sb["seconds_filter"], "orth": sb["seconds_orth"],
-                                                 "rr": sb["seconds_rr"]},
+        sb = whole_solve(pfe, torch, arrays, wl, method=1)
+        s3 = sb["stats"]
+        line["block_lanczos"] = {"value": sb["seconds"], "unit": "s", "n_found": sb["n_found"],
+                                 "matvecs": s3["matvecs"], "restarts": s3["restarts"], "basis": s3["basis"],
+                                 "block": s3["width"], "degree": s3["degree"],
+                                 "max_rel_residual": sb["max_rel_residual"],
+                                 "breakdown_s": {"filter": s3["seconds_filter"], "orth": s3["seconds_orth"],
+                                                 "rr": s3["seconds_rr"]},
                                  "note": "thick-restart block Lanczos on p(Ht), then Rayleigh-Ritz with H "
-                                         "(the paper's block Krylov-Schur solver); timed once after the "
+                                         "(the paper's block Krylov-Schur solver); one solve after the timed "
                                          "subspace-iteration steps"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = OracleSample(wl)
+        for _ in range(2):
+            smp.step()
+        smp.step_times.pop(0)  # the first step warms the processes up
+        est, t_mv, t_dense, dense = smp.estimate(work_live)
+        smp.close()
+        line["cpu_baseline"] = {"value": est, "unit": "s", "cores": smp.cores, "kind": "oracle",
+                                "sample": smp.describe() + f"; extrapolated to this solve's work "
+                                                           f"({st['iterations']} iterations, {st['matvecs']} "
+                                                           f"products with H, ~{dense:.3g} dense flops)",
+                                "extrapolated": True}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -380,7 +650,7 @@ def run_native(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=15)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -388,6 +658,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-block-lanczos", dest="block_lanczos", action="store_false")
     args = ap.parse_args()
+    if args.steps < 1 or args.warmup < 0:
+        ap.error("--steps must be >= 1 and --warmup >= 0")
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

@@ -166,7 +166,7 @@ pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs,
  *   kind 0: the piecewise quadratic filter of eq. (fct_f) with margin eps and rate r (eq. (thresh));
  *   kind 1: the Dirac filter of eq. (cheby-delta.1), centred so that rho(xi) = rho(eta), with phi;
  * damping 0 none, 1 Jackson, 2 Lanczos (Sec. 2.3).  degree 0: the automatic degree (smallest
- * qualifying, as the solver picks it), else that degree.  *m_out receives the degree;
+ * qualifying, as the solver picks it), else that degree (at most 60000, PFE_E_ARG above).  *m_out receives the degree;
  * coeffs[0..m] (host, cap doubles; may be NULL to query m) the damped Chebyshev coefficients.
  * PFE_E_ARG for an invalid interval or parameter or when no degree <= 60000 qualifies;
  * PFE_E_CAPACITY if cap < m + 1 (m still stored). */
@@ -180,6 +180,23 @@ pfe_status pfe_design_filter(int kind, double xi, double eta, double eps, double
  * PFE_E_CAPACITY: the subspace was too narrow to certify completeness (raise PFE_P_WIDTH);
  * PFE_E_NOCONV: the iteration limit was hit (partial results are kept). */
 pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found);
+
+/* The same filtered subspace iteration one outer iteration at a time (Alg. 4: each pass of its
+ * loop is one application of p(Ht) to the active block, CholQR2 against the locked vectors,
+ * Rayleigh-Ritz with H, residuals and locking).  pfe_solve is exactly
+ *     pfe_solve_begin; do pfe_solve_iterate until *done; pfe_solve_end.
+ * pfe_solve_begin: the set-up of pfe_solve (lambda_max bound and filter design if not yet done,
+ *   count estimate, width, buffers, random start block and its orthonormalisation).  METHOD 0
+ *   only (PFE_E_ARG otherwise); PFE_E_STATE without an interval.
+ * pfe_solve_iterate: one outer iteration; *done (may be NULL) becomes 1 once the termination test
+ *   of pfe_solve holds or the iteration limit is reached, after which further calls do nothing.
+ *   Returns when the iteration's device work has finished.  On an error the solve is over.
+ * pfe_solve_end: the results, as pfe_solve returns them.  Called before *done, it ends the solve
+ *   early: the eigenpairs locked so far are the results and the status is PFE_E_NOCONV.
+ * pfe_solve_iterate and pfe_solve_end return PFE_E_STATE when no stepwise solve is in progress. */
+pfe_status pfe_solve_begin(pfe_ctx *ctx);
+pfe_status pfe_solve_iterate(pfe_ctx *ctx, int32_t *done);
+pfe_status pfe_solve_end(pfe_ctx *ctx, int32_t *n_found);
 
 /* Copy the results of the last pfe_solve: lambda[cap] ascending, vecs n x cap column-major
  * (ld = n, unit 2-norm, mass-weighted coordinates q of eq. (3)), resid[cap] = ||H v - lambda v||
@@ -220,7 +237,14 @@ typedef struct {
                                   7-9: the rank-1 form), -1 if none ran */
   int32_t filter_shape_f32;    /* the same for the FP32 filter step */
   int32_t slices;              /* pfe_solve_sliced: number of slices (0 for the other solves) */
+  int32_t active;              /* stepwise solve in progress: columns still iterating (0 otherwise) */
+  int32_t locked;              /* stepwise solve in progress: converged pairs locked so far (0 otherwise) */
+  int32_t cholqr_shifts;       /* Cholesky factorisations of CholQR2 that broke down and were repeated
+                                  with the shift of the retry (numerically rank-deficient blocks) */
 } pfe_stats;
+/* Between pfe_solve_begin and pfe_solve_end the counters iterations, matvecs, width, degree,
+ * active, locked and kernel_launches describe the solve in progress; the other fields are those of
+ * the last finished solve. */
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *stats);
 
 /* ---------------------------------------------------------------------------------------
@@ -270,9 +294,25 @@ pfe_status pfe_chain_springs(pfe_ctx *ctx, int64_t nbonds, const int32_t *bi, co
  * Preconditions: the context already holds the FP64 filter operator for its current transform --
  * any earlier pfe_filter_apply, pfe_estimate or pfe_solve on it builds it (else PFE_E_STATE).
  * coeffs: host array of m + 1 coefficients (required); X, Y: device pointers, column-major n x k,
- * ld >= n, float64; stream as in pfe_filter_apply. */
+ * ld >= n, float64; stream as in pfe_filter_apply.  Given a stream other than the context's, the
+ * call first waits on the host for the context's stream, where the filter operator was built.
+ * It runs the kernel shape that pfe_filter_apply tuned for this column count (shape 0 before any
+ * tuning), and does not time shapes itself. */
 pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeffs, int32_t k, const double *X,
                                     int64_t ldx, double *Y, int64_t ldy, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Machine measurement (no counterpart in the paper)
+ * ------------------------------------------------------------------------------------- */
+
+/* The FP64 FMA throughput this GPU sustains, the ceiling of every FP64 step of the method (the
+ * filter step on GB300 is bound by the FP64 pipe).  Launches, on `stream` (a cudaStream_t, NULL =
+ * the legacy default stream), a kernel in which 8 CTAs of 256 threads per SM each advance 8
+ * independent FMA chains `iters` times; the first launch warms up, the next `reps` are timed with
+ * CUDA events on that stream.  *tflops receives 2 x FMAs / seconds / 1e12.  `sink` is one device
+ * double the kernel writes only if a chain ends at a value it cannot reach (it keeps the chains
+ * from being optimised away).  PFE_E_ARG for iters < 1, reps < 1, NULL sink or tflops. */
+pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stream, double *sink, double *tflops);
 
 /* ---------------------------------------------------------------------------------------
  * Batched solves of independent samples (the realisations H_1 .. H_8 of Sec. 4.2)

@@ -41,7 +41,8 @@ EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", 
            "pfe_get_param", "pfe_set_interval", "pfe_estimate", "pfe_get_filter", "pfe_solve",
            "pfe_get_eigenpairs", "pfe_get_stats", "pfe_filter_apply", "pfe_filter_adjoint",
            "pfe_chain_springs", "pfe_solve_batch", "pfe_filter_apply_noalloc", "pfe_participation_ratio",
-           "pfe_plane_wave_content", "pfe_solve_sliced", "pfe_design_filter")
+           "pfe_plane_wave_content", "pfe_solve_sliced", "pfe_design_filter", "pfe_solve_begin",
+           "pfe_solve_iterate", "pfe_solve_end", "pfe_probe_fp64_fma")
 
 
 class PfeError(RuntimeError):
@@ -61,7 +62,8 @@ class PfeStats(ctypes.Structure):
                 ("filter_col_steps", ctypes.c_int64), ("filter_col_steps_f32", ctypes.c_int64),
                 ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64),
                 ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32), ("filter_shape_f64", ctypes.c_int32),
-                ("filter_shape_f32", ctypes.c_int32), ("slices", ctypes.c_int32)]
+                ("filter_shape_f32", ctypes.c_int32), ("slices", ctypes.c_int32), ("active", ctypes.c_int32),
+                ("locked", ctypes.c_int32), ("cholqr_shifts", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -91,6 +93,10 @@ def load(path: str | None = None):
         "pfe_estimate": (ctypes.c_int, [_P, _P, _P]),
         "pfe_get_filter": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P]),
         "pfe_solve": (ctypes.c_int, [_P, _P]),
+        "pfe_solve_begin": (ctypes.c_int, [_P]),
+        "pfe_solve_iterate": (ctypes.c_int, [_P, _P]),
+        "pfe_solve_end": (ctypes.c_int, [_P, _P]),
+        "pfe_probe_fp64_fma": (ctypes.c_int, [_I32, _I32, _P, _P, _P]),
         "pfe_get_eigenpairs": (ctypes.c_int, [_P, _I32, _P, _P, _P, _U32]),
         "pfe_get_stats": (ctypes.c_int, [_P, _P]),
         "pfe_filter_apply": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _I64, _P, _I64, ctypes.c_int, _P]),
@@ -231,9 +237,31 @@ def pfe_solve(ctx, raise_on_error=True):
     return nf.value, st
 
 
+def pfe_solve_begin(ctx):
+    """Set-up of a stepwise subspace-iteration solve."""
+    _check(load().pfe_solve_begin(ctx), ctx)
+
+
+def pfe_solve_iterate(ctx) -> bool:
+    """One outer iteration; returns True once the solve has ended."""
+    done = ctypes.c_int32(0)
+    _check(load().pfe_solve_iterate(ctx, ctypes.byref(done)), ctx)
+    return bool(done.value)
+
+
+def pfe_solve_end(ctx, raise_on_error=True):
+    """Results of a stepwise solve. Returns (n_found, status)."""
+    nf = ctypes.c_int32(0)
+    st = load().pfe_solve_end(ctx, ctypes.byref(nf))
+    if raise_on_error:
+        _check(st, ctx)
+    return nf.value, st
+
+
 def pfe_get_eigenpairs(ctx, n, cap, vecs_out=None):
-    """Host copies (lambda, vecs n x cap column-major as an (n, cap) array, resid); with a
-    torch CUDA tensor `vecs_out` (column-major n x cap storage) the vectors go to the device."""
+    """Host copies (lambda, vecs n x cap column-major as an (n, cap) array, resid); with a torch
+    tensor `vecs_out` (column-major n x cap storage, e.g. shape (cap, n)) the vectors go there: to the
+    device for a CUDA tensor (or an integer device pointer), to host memory (e.g. pinned) for a CPU one."""
     lam = np.zeros(cap)
     res = np.zeros(cap)
     if vecs_out is None:
@@ -241,7 +269,8 @@ def pfe_get_eigenpairs(ctx, n, cap, vecs_out=None):
         st = load().pfe_get_eigenpairs(ctx, cap, lam.ctypes.data, vecs.ctypes.data, res.ctypes.data, 0)
         _check(st, ctx)
         return lam, vecs.T, res
-    st = load().pfe_get_eigenpairs(ctx, cap, lam.ctypes.data, _dptr(vecs_out), res.ctypes.data, PFE_DEVICE_PTRS)
+    flags = PFE_DEVICE_PTRS if getattr(vecs_out, "is_cuda", True) else 0
+    st = load().pfe_get_eigenpairs(ctx, cap, lam.ctypes.data, _dptr(vecs_out), res.ctypes.data, flags)
     _check(st, ctx)
     return lam, vecs_out, res
 
@@ -328,6 +357,14 @@ def pfe_solve_sliced(ctx, edges=None, raise_on_error=True):
     if raise_on_error and st != PFE_OK:
         _check(st, ctx)
     return nf.value, st
+
+
+def pfe_probe_fp64_fma(iters, reps, sink, stream=None) -> float:
+    """Measured FP64 FMA throughput (TFLOP/s) of this GPU; sink: a device tensor of >= 1 double."""
+    t = ctypes.c_double(0)
+    _check(load().pfe_probe_fp64_fma(int(iters), int(reps), _stream(stream), _dptr(sink), ctypes.byref(t)), None,
+           "pfe_probe_fp64_fma failed")
+    return t.value
 
 
 DAMPING_KINDS = {"none": 0, "jackson": 1, "lanczos": 2}

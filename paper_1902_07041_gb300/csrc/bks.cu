@@ -85,6 +85,7 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   ctx->has_result = false;
   ctx->n_found = 0;
   ctx->stats = pfe_stats{};
+  ctx->shift_count = 0;
   PFE_TRY(solver_ensure_filter(ctx));
   PFE_TRY(solver_ensure_hs(ctx, false));
   const int64_t n = ctx->n;
@@ -337,6 +338,7 @@ pfe_status bks_solve(pfe_ctx *ctx, int32_t *n_found) {
   for (double r : sel_res) mr = std::max(mr, r / ctx->lmax);
   o.max_residual = mr;
   o.fp64_sweeps = 0;
+  o.cholqr_shifts = ctx->shift_count;
   o.status = (int32_t)result;
   o.kernel_launches = launch_count() - ctx->launch_base;
   o.filter_launches = f_launch;

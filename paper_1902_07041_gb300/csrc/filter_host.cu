@@ -253,7 +253,9 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
 extern "C" pfe_status pfe_design_filter(int kind, double xi, double eta, double eps, double r, double phi, int damping,
                                         int32_t degree, int32_t cap, int32_t *m_out, double *coeffs) {
   using namespace pfe;
-  if (!m_out || (kind != 0 && kind != 1) || (damping < 0 || damping > 2) || degree < 0) return PFE_E_ARG;
+  // explicit degrees share the automatic search's limit of 60000
+  if (!m_out || (kind != 0 && kind != 1) || (damping < 0 || damping > 2) || degree < 0 || degree > 60000)
+    return PFE_E_ARG;
   if (!(xi >= -1.0 && xi < eta && eta <= 1.0)) return PFE_E_ARG;
   if (kind == 0 && !(eps > 0.0 && r > 0.0 && r < 1.0)) return PFE_E_ARG;
   if (kind == 1 && !(phi > 0.0 && phi < 1.0)) return PFE_E_ARG;
@@ -264,7 +266,7 @@ extern "C" pfe_status pfe_design_filter(int kind, double xi, double eta, double 
   }
   *m_out = m;
   if (!coeffs) return PFE_OK;
-  if (cap < m + 1) return PFE_E_CAPACITY;
+  if ((int64_t)cap < (int64_t)m + 1) return PFE_E_CAPACITY;
   std::vector<double> c;
   if (kind == 0) {
     std::vector<double> gam, g;

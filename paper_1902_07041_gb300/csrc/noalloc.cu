@@ -58,23 +58,24 @@ extern "C" pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const do
   double *base = g_scratch_ptr[ctx->device];
   double *Xr = base, *Yr = base + n * ld, *b0 = base + 2 * n * ld, *b1 = base + 3 * n * ld;
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
-  // the previous call's contents stay in the array: zero the padding columns the kernels touch
-  launch_zero<double>(base, need, s);
-  launch_colmajor_to_rowmajor<double>(n, k, X, ldx, Xr, ld, s);
-  const Bsr<double> A{ctx->N, ctx->rp.as<int32_t>(), ctx->ci.as<int32_t>(), ctx->Hs64.as<double>()};
-  if (m == 0) {
-    launch_axpby<double>(n, k, coeffs[0], Xr, ld, 0.0, Yr, ld, s);
-  } else {
-    launch_bsr_step<double>(A, MODE_FIRST, k, ld, Xr, nullptr, b0, Yr, 0.5, 0.0, coeffs[0], coeffs[1], s);
-    const double *tprev = Xr;
-    double *tcur = b0;
-    for (int32_t j = 1; j < m; ++j) {
-      double *out = (tprev == Xr) ? b1 : const_cast<double *>(tprev);
-      launch_bsr_step<double>(A, MODE_STEP, k, ld, tcur, tprev, out, Yr, 1.0, -1.0, 0.0, coeffs[j + 1], s);
-      tprev = tcur;
-      tcur = out;
+  // the filter operator was built on the context's stream: wait for it (a host wait, no allocation)
+  if (s != ctx->stream) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  }
+  // The array keeps the previous call's contents.  Columns are independent, so only the padding
+  // columns k .. ld-1 of the four blocks (read by the vector lanes, never copied out) are cleared.
+  if (ld > k) {
+    for (double *p : {Xr, Yr, b0, b1}) {
+      cudaError_t e = cudaMemset2DAsync(p + k, (size_t)ld * sizeof(double), 0, (size_t)(ld - k) * sizeof(double),
+                                        (size_t)n, s);
+      if (e != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, std::string("cudaMemset2DAsync: ") + cudaGetErrorString(e));
     }
   }
+  launch_colmajor_to_rowmajor<double>(n, k, X, ldx, Xr, ld, s);
+  // the filter driver of pfe_filter_apply (rank-1 operator when built, STEP / STEP_ACC launches),
+  // without its shape autotuner, which would synchronise the stream
+  PFE_TRY(solver_filter64_rows(ctx, coeffs, m, k, ld, Xr, Yr, b0, b1, s, false));
   launch_rowmajor_to_colmajor<double>(n, k, Yr, ld, Y, ldy, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, std::string("filter_apply_noalloc: ") + cudaGetErrorString(e));

@@ -193,6 +193,7 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
 // --------------------------------------------------------------------------------------
 struct SolveState {
   bool fp32 = false, use64 = true, was64 = true, done = false, timed_filter = true, timed32 = false;
+  bool active = false;  // a stepwise solve (pfe_solve_begin .. pfe_solve_end) is in progress
   int32_t q = 0, act = 0, nl = 0, it = 0, prev_count = -1, fp64_sweeps = 0;
   int32_t k64 = 0;  // mixed precision: the first k64 active columns use the FP64 filter
   int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
@@ -273,6 +274,7 @@ struct pfe_ctx {
   // results
   bool has_result = false;
   int32_t n_found = 0;
+  int32_t shift_count = 0;  // shifted Cholesky factorisations since the current solve began
   pfe::DBuf L;          // locked vectors, row-major n x ldq
   int64_t ldq = 0;
   std::vector<int32_t> result_cols;  // columns of L in ascending eigenvalue order
@@ -300,6 +302,10 @@ pfe_status solver_window(pfe_ctx *ctx, double *out);
 pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result,
                           bool *shifted = nullptr);
 pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1);
+// Y = sum_j coef[j] T_j(Ht) X on row-major n x ld blocks with the FP64 filter operator (its rank-1 form
+// when built), on stream s; tune = false runs the already tuned kernel shape without timing candidates
+pfe_status solver_filter64_rows(pfe_ctx *ctx, const double *coef, int32_t m, int32_t k, int64_t ld, const double *X,
+                                double *Y, double *b0, double *b1, cudaStream_t s, bool tune);
 double solver_now();
 pfe_status solver_ensure_lmax(pfe_ctx *ctx);
 Bsr<double> solver_bsr_H(const pfe_ctx *ctx);     // H

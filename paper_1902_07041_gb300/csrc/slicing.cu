@@ -181,6 +181,7 @@ extern "C" pfe_status pfe_solve_sliced(pfe_ctx *ctx, int32_t nedges, const doubl
     sum.filter_col_steps_f32 += o.filter_col_steps_f32;
     sum.seconds_filter_f32 += o.seconds_filter_f32;
     sum.restarts += o.restarts;
+    sum.cholqr_shifts += o.cholqr_shifts;
     sum.width = std::max(sum.width, o.width);
     sum.basis = std::max(sum.basis, o.basis);
     sum.degree = std::max(sum.degree, o.degree);

@@ -84,15 +84,17 @@ pfe_status check_launch(pfe_ctx *ctx, const char *what) {
 // Y = sum_j coef[j] T_j(Ht) X with A = (2/d)(H - cI) = 2 Ht:
 //   t_1 = A t_0 / 2, t_{j+1} = A t_j - t_{j-1}; y accumulated in the same launch.
 // X is read-only; b0, b1 are two scratch multivectors of the same shape.
+// tune = false skips the shape autotuner (it synchronises the stream to time the candidates); the
+// launches then take the shape already tuned for this type and column count, else shape 0.
 template <typename T>
 pfe_status run_filter(pfe_ctx *ctx, const Bsr<T> &A, const double *coef, int32_t m, int32_t k, int64_t ld, const T *X,
-                      T *Y, T *b0, T *b1, cudaStream_t s) {
+                      T *Y, T *b0, T *b1, cudaStream_t s, bool tune = true) {
   if (k <= 0) return PFE_OK;
   if (m == 0) {
     launch_axpby<T>(ctx->n, k, (T)coef[0], X, ld, T(0), Y, ld, s);
     return check_launch(ctx, "filter (degree 0)");
   }
-  tune_step<T>(A, k, ld, X, b1, s);  // b1 is free until the second step
+  if (tune) tune_step<T>(A, k, ld, X, b1, s);  // b1 is free until the second step
   launch_bsr_step<T>(A, MODE_FIRST, k, ld, X, nullptr, b0, Y, T(0.5), T(0), (T)coef[0], (T)coef[1], s);
   const T *tprev = X;
   T *tcur = b0;
@@ -360,6 +362,7 @@ pfe_status chol_factor(pfe_ctx *ctx, double *G, double *Rinv, int32_t k, bool *s
   *shifted = false;
   if (hinfo != 0) {
     *shifted = true;
+    ++ctx->shift_count;
     double tr = 0.0;
     for (int32_t i = 0; i < k; ++i) tr += hG[(size_t)i * k + i];
     const double sh = 11.0 * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
@@ -449,6 +452,7 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   ctx->has_result = false;
   ctx->n_found = 0;
   ctx->stats = pfe_stats{};
+  ctx->shift_count = 0;
   st.fp32 = ctx->p_precision == 1;
   PFE_TRY(ensure_filter(ctx));
   PFE_TRY(ensure_hs(ctx, st.fp32));
@@ -714,6 +718,7 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
   o.seconds_rr = st.t_rr;
   o.max_residual = maxres;
   o.fp64_sweeps = st.fp64_sweeps;
+  o.cholqr_shifts = ctx->shift_count;
   o.status = (int32_t)st.result;
   o.kernel_launches = launch_count() - ctx->launch_base;
   o.filter_launches = st.f_launch;
@@ -734,7 +739,8 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
     }
   if (n_found) *n_found = ctx->n_found;
   if (st.result == PFE_E_CAPACITY) return pfe_fail(ctx, st.result, "every Ritz vector lies in [a, b]: raise PFE_P_WIDTH");
-  if (st.result == PFE_E_NOCONV) return pfe_fail(ctx, st.result, "iteration limit reached");
+  if (st.result == PFE_E_NOCONV)
+    return pfe_fail(ctx, st.result, st.it >= ctx->p_max_iters ? "iteration limit reached" : "solve ended before convergence");
   return PFE_OK;
 }
 
@@ -943,6 +949,10 @@ pfe_status solver_cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64
 }
 pfe_status solver_filter64(pfe_ctx *ctx, int32_t k, int64_t ld, const double *X, double *Y, double *b0, double *b1) {
   return run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k, ld, X, Y, b0, b1, ctx->stream);
+}
+pfe_status solver_filter64_rows(pfe_ctx *ctx, const double *coef, int32_t m, int32_t k, int64_t ld, const double *X,
+                                double *Y, double *b0, double *b1, cudaStream_t s, bool tune) {
+  return run_filter<double>(ctx, bsr_Hs64(ctx), coef, m, k, ld, X, Y, b0, b1, s, tune);
 }
 double solver_now() { return now_s(); }
 pfe_status solver_ensure_lmax(pfe_ctx *ctx) { return ensure_lmax(ctx); }
@@ -1369,23 +1379,72 @@ pfe_status pfe_get_filter(pfe_ctx *ctx, int32_t cap, int32_t *m, double *coeffs,
   return PFE_OK;
 }
 
+pfe_status pfe_solve_begin(pfe_ctx *ctx) {
+  if (!ctx) return PFE_E_ARG;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+  if (ctx->p_method != 0)
+    return pfe_fail(ctx, PFE_E_ARG, "the stepwise solve runs the filtered subspace iteration (METHOD 0)");
+  ctx->solve.active = false;
+  PFE_TRY(solve_setup(ctx));
+  ctx->solve.active = true;
+  return PFE_OK;
+}
+
+pfe_status pfe_solve_iterate(pfe_ctx *ctx, int32_t *done) {
+  if (!ctx) return PFE_E_ARG;
+  SolveState &st = ctx->solve;
+  if (!st.active) return pfe_fail(ctx, PFE_E_STATE, "no stepwise solve in progress (pfe_solve_begin)");
+  if (!st.done) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
+    cudaEventRecord(st.ev[0], ctx->stream);
+    pfe_status r = solve_filter(ctx);
+    if (r == PFE_OK) r = solve_after_filter(ctx);
+    if (r != PFE_OK) {
+      st.active = false;
+      return r;
+    }
+  }
+  if (done) *done = st.done ? 1 : 0;
+  return PFE_OK;
+}
+
+pfe_status pfe_solve_end(pfe_ctx *ctx, int32_t *n_found) {
+  if (!ctx) return PFE_E_ARG;
+  SolveState &st = ctx->solve;
+  if (!st.active) return pfe_fail(ctx, PFE_E_STATE, "no stepwise solve in progress (pfe_solve_begin)");
+  st.active = false;
+  if (!st.done) {  // ended early: the pairs locked so far are the results
+    st.result = PFE_E_NOCONV;
+    st.done = true;
+  }
+  return solve_finish(ctx, n_found);
+}
+
 pfe_status pfe_solve(pfe_ctx *ctx, int32_t *n_found) {
   if (!ctx) return PFE_E_ARG;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return pfe_fail(ctx, PFE_E_CUDA, "cudaSetDevice failed");
   if (ctx->p_method == 1) return bks_solve(ctx, n_found);
-  SolveState &st = ctx->solve;
-  PFE_TRY(solve_setup(ctx));
-  while (!st.done) {
-    cudaEventRecord(st.ev[0], ctx->stream);
-    PFE_TRY(solve_filter(ctx));
-    PFE_TRY(solve_after_filter(ctx));
-  }
-  return solve_finish(ctx, n_found);
+  PFE_TRY(pfe_solve_begin(ctx));
+  int32_t done = 0;
+  while (!done) PFE_TRY(pfe_solve_iterate(ctx, &done));
+  return pfe_solve_end(ctx, n_found);
 }
 
 pfe_status pfe_get_stats(const pfe_ctx *ctx, pfe_stats *st) {
   if (!ctx || !st) return PFE_E_ARG;
   *st = ctx->stats;
+  st->active = st->locked = 0;
+  const SolveState &ss = ctx->solve;
+  if (ss.active) {  // a stepwise solve in progress
+    st->iterations = ss.it;
+    st->matvecs = ss.matvecs;
+    st->width = ss.q;
+    st->degree = ctx->m;
+    st->active = ss.act;
+    st->locked = ss.nl;
+    st->kernel_launches = launch_count() - ctx->launch_base;
+    st->cholqr_shifts = ctx->shift_count;
+  }
   return PFE_OK;
 }
 

@@ -112,7 +112,21 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.pfe_set_param(None, pfe.PFE_P_TOL, 1e-8) == pfe.PFE_E_ARG
     assert lib.pfe_set_interval(None, 0.0, 1.0) == pfe.PFE_E_ARG
     assert lib.pfe_solve(None, None) == pfe.PFE_E_ARG
+    assert lib.pfe_solve_begin(None) == pfe.PFE_E_ARG
+    assert lib.pfe_solve_iterate(None, None) == pfe.PFE_E_ARG
+    assert lib.pfe_solve_end(None, None) == pfe.PFE_E_ARG
+    assert lib.pfe_get_stats(None, None) == pfe.PFE_E_ARG
     lib.pfe_destroy(None)
+
+
+def test_fp64_probe_rejects_bad_arguments_before_any_launch(lib):
+    import ctypes
+
+    t = ctypes.c_double(0)
+    assert lib.pfe_probe_fp64_fma(0, 1, None, 8, ctypes.byref(t)) == pfe.PFE_E_ARG
+    assert lib.pfe_probe_fp64_fma(10, 0, None, 8, ctypes.byref(t)) == pfe.PFE_E_ARG
+    assert lib.pfe_probe_fp64_fma(10, 1, None, None, ctypes.byref(t)) == pfe.PFE_E_ARG
+    assert lib.pfe_probe_fp64_fma(10, 1, None, 8, None) == pfe.PFE_E_ARG
 
 
 _RATES = {"0.1": 0.1, "sqrt(0.1)": 0.1 ** 0.5, "0.1^(1/4)": 0.1 ** 0.25}
@@ -161,3 +175,10 @@ def test_library_filter_design_rejects_bad_input(lib):
         pfe.pfe_design_filter("pq", -0.9, -0.8, eps=0.01, r=1.5)  # r outside (0, 1)
     with pytest.raises(pfe.PfeError):
         pfe.pfe_design_filter("dirac", -0.9, -0.8, phi=0.0)
+    # explicit degrees share the automatic search's limit of 60000
+    for deg in (60001, 2 ** 31 - 1):
+        with pytest.raises(pfe.PfeError) as e:
+            pfe.pfe_design_filter("pq", -0.9, -0.8, eps=0.01, r=0.3, degree=deg)
+        assert e.value.status == pfe.PFE_E_ARG
+    m, c = pfe.pfe_design_filter("pq", -0.9, -0.8, eps=0.01, r=0.3, degree=60000)
+    assert m == 60000 and c.size == 60001

@@ -337,18 +337,6 @@ def test_solve_block_lanczos_n1000():
     _solve_and_check(glassgen.generate(1000, 0), 0.02, 0.05, METHOD=1, BLOCK=32)
 
 
-def test_solve_capacity_error():
-    g = glassgen.generate(300, 5)
-    ctx, _ = make_ctx(g, WIDTH=8)
-    try:
-        lmax, _ = pfe.pfe_estimate(ctx)
-        pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.3 * lmax)
-        nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
-        assert st in (pfe.PFE_E_CAPACITY, pfe.PFE_E_NOCONV)
-    finally:
-        pfe.pfe_destroy(ctx)
-
-
 @pytest.mark.parametrize("threads", [0, 1, 3])
 def test_solve_batch_equals_solo(threads):
     """Batched lockstep solve (one persistent filter launch per step over all samples, replayed from

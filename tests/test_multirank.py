@@ -57,3 +57,25 @@ def test_reference_arm_nonzero_rank_does_no_work():
                         "--warmup", "0", "--workload", "glass-n1k-fp64"], env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_runs_the_oracle_only():
+    """The reference arm on a small workload: one JSON line whose per-step time covers the timed
+    steps, measured on the host cores with the oracle; the GPU library is never loaded."""
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '2', '--warmup', '1', "
+            "'--workload', 'glass-n1k-fp64']; runpy.run_path('bench.py', run_name='__main__'); "
+            "maps = open('/proc/self/maps').read(); print('LIBPFE_LOADED' if 'libpfe' in maps else 'LIBPFE_ABSENT')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert lines[-1] == "LIBPFE_ABSENT"
+    import json
+
+    rec = json.loads(lines[-2])
+    assert rec["impl"] == "reference" and rec["steps"] == 2 and rec["warmup"] == 1
+    assert rec["unit"] == "s" and rec["higher_is_better"] is False and rec["value"] > 0
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
+    assert rec["cpu_baseline"]["value"] == rec["value"]
+    assert rec["ms_per_step"] * rec["steps"] <= 1e3 * rec["timed_wall_s"] * 1.001 + 1.0
+    full = rec["cpu_baseline"]["oracle_full_solve_n1000"]
+    assert full["status"] == 0 and full["n_found"] == 144  # the exact count of [0.02, 0.05] lambda_max

@@ -151,6 +151,56 @@ def test_cheb_filter_vs_eigendecomposition(small_glass):
 
 
 # ------------------------------------------------------------------ model invariants
+def _residuals_ld(H, lam, V, ld):
+    """or_residuals called directly with a leading dimension ld >= n (V: ld x k, column-major)."""
+    lam = np.ascontiguousarray(lam, np.float64)
+    V = np.asfortranarray(V, np.float64)
+    r = np.zeros(V.shape[1])
+    oracle._load().or_residuals(H.handle, V.shape[1], oracle._ptr(lam), oracle._ptr(V), ld, oracle._ptr(r))
+    return r
+
+
+def test_residuals_diagonal_closed_form():
+    """Alg. 3's residual r = ||H v - lambda v|| on a diagonal H, where it has a closed form:
+    for v = alpha e_i + beta e_j, H v - mu v = alpha (d_i - mu) e_i + beta (d_j - mu) e_j, so
+    r = sqrt(alpha^2 (d_i - mu)^2 + beta^2 (d_j - mu)^2); for a unit vector e_i it is |d_i - mu|.
+    The columns sit in a block whose leading dimension exceeds n, with NaN in the padding rows: a
+    stride slip reads them; a dropped square root, a wrong sign or a wrong index changes the value."""
+    n, ld = 7, 11
+    d = np.array([0.5, -1.25, 2.0, 3.75, -0.125, 1.5, 4.0])
+    H = oracle.csr_diagonal(d)
+    cols = [(2, 1.0, None, 0.0, 0.75), (0, 1.0, None, 0.0, -2.0), (4, 0.6, 6, 0.8, 1.0), (1, 3.0, 5, -4.0, 0.0)]
+    V = np.full((ld, len(cols)), np.nan)
+    V[:n] = 0.0
+    lam, want = [], []
+    for c, (i, a, j, b, mu) in enumerate(cols):
+        V[i, c] = a
+        if j is not None:
+            V[j, c] = b
+        lam.append(mu)
+        want.append(math.hypot(a * (d[i] - mu), 0.0 if j is None else b * (d[j] - mu)))
+    r = _residuals_ld(H, lam, V, ld)
+    assert np.all(np.isfinite(r))
+    assert np.allclose(r, want, rtol=4e-16, atol=0)
+    assert r[0] == abs(d[2] - 0.75) and r[1] == abs(d[0] + 2.0)  # unit vectors: exact
+    # the Python wrapper (leading dimension n) on the same columns
+    assert np.allclose(oracle.residuals(H, lam, V[:n]), want, rtol=4e-16, atol=0)
+
+
+def test_residuals_of_exact_eigenpairs(small_glass):
+    """Exact eigenpairs of the glass Hessian (LAPACK) have residual at rounding level, and a shifted
+    eigenvalue lambda + delta gives exactly |delta| (||v|| = 1, H v = lambda v)."""
+    _, H, Hd = small_glass
+    w, U = np.linalg.eigh(Hd)
+    sel = [0, 5, 100, U.shape[1] - 1]
+    nrm = np.abs(w).max()
+    r = oracle.residuals(H, w[sel], U[:, sel])
+    assert np.all(r <= 1e-13 * nrm)
+    delta = np.array([1e-3, -2e-2, 0.5, -1.0]) * nrm
+    r2 = oracle.residuals(H, w[sel] + delta, U[:, sel])
+    assert np.allclose(r2, np.abs(delta), rtol=1e-10, atol=1e-13 * nrm)
+
+
 def test_hessian_invariants(small_glass):
     g, H, A = small_glass
     assert np.array_equal(A, A.T)  # bitwise symmetric

@@ -54,11 +54,34 @@ def test_noalloc_filter_matches_allocating_filter_twice():
         ref1 = _filter(ctx, coef, X1, False)
         ref2 = _filter(ctx, coef, X2, False)
         tol = 1e-11 * np.abs(coef).sum()
+        # the allocating filter itself against the oracle's Alg. 2 (c = d = lambda_max / 2)
+        H = oracle.csr_from_springs(g)
+        assert np.max(np.abs(ref1 - oracle.cheb_filter(H, 0.1, 0.1, coef, X1))) <= tol * np.abs(X1).max()
         for _ in range(2):  # two calls in a row share (and reuse) the fixed array
             y1 = _filter(ctx, coef, X1, True)
             assert np.max(np.abs(y1 - ref1)) <= tol * np.abs(X1).max()
             y2 = _filter(ctx, coef, X2, True)
             assert np.max(np.abs(y2 - ref2)) <= tol * np.abs(X2).max()
+            assert np.max(np.abs(y1 - oracle.cheb_filter(H, 0.1, 0.1, coef, X1))) <= tol * np.abs(X1).max()
+        # a caller stream other than the context's, right after an allocating call that builds the
+        # filter operator on the context's stream (a fresh context: nothing built before)
+        ctx3 = pfe.pfe_create(g.n_atoms, *pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat), g.mass)
+        try:
+            pfe.pfe_set_param(ctx3, pfe.PFE_P_LAMBDA_MAX, 0.2)
+            n, k = X1.shape
+            Xd = torch.from_numpy(np.ascontiguousarray(X1.T)).cuda()
+            Ya = torch.full((k, n), float("nan"), device="cuda", dtype=torch.float64)
+            Yb = torch.full((k, n), float("nan"), device="cuda", dtype=torch.float64)
+            torch.cuda.synchronize()
+            side = torch.cuda.Stream()
+            pfe.pfe_filter_apply(ctx3, len(coef) - 1, coef, k, Xd, n, Ya, n, pfe.PFE_F64)  # context stream
+            pfe.pfe_filter_apply_noalloc(ctx3, len(coef) - 1, coef, k, Xd, n, Yb, n, stream=side)
+            side.synchronize()
+            torch.cuda.synchronize()
+            assert np.max(np.abs(Yb.cpu().numpy().T - ref1)) <= tol * np.abs(X1).max()
+            assert np.max(np.abs(Ya.cpu().numpy().T - ref1)) <= tol * np.abs(X1).max()
+        finally:
+            pfe.pfe_destroy(ctx3)
         # sizes beyond the fixed array are rejected with a clear error
         big = glassgen.generate(20000, 2)
         rp, ci, vals = pfe.pfe_springs_to_bsr(big.n_atoms, big.bi, big.bj, big.k, big.rhat)
