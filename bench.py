@@ -54,7 +54,9 @@ DEFAULT = "glass-n100k-fp64"
 # and locked column counts of each iteration.  The reference arm scales the oracle's measured rates
 # by these counts; the native arm prints its own counts beside them.
 SOLVE_WORK = {
-    "glass-n100k-fp64": dict(width=994, degree=417, iterations=13, matvecs=4_178_687, active=None, locked=None),
+    "glass-n100k-fp64": dict(width=994, degree=417, iterations=13, matvecs=4_178_687,
+                             active=[994] * 7 + [872, 620, 478, 396, 342, 307],
+                             locked=[0] * 7 + [122, 374, 516, 598, 652, 687]),
 }
 
 # DRAM traffic per launch of the dominant kernel, measured by ncu (dram__bytes_read.sum +

@@ -109,7 +109,10 @@ enum {
                                of Tables 1-3) */
   PFE_P_DIRAC_CUT = 28,     /* Dirac filter with METHOD 1: Ritz values of rho(Ht) >= DIRAC_CUT x rho(xi) are
                                wanted (default 0.9) */
-  PFE_P_SLICE_TARGET = 29   /* pfe_solve_sliced: eigenvalues per slice the automatic edges aim at (default 1000) */
+  PFE_P_SLICE_TARGET = 29,  /* pfe_solve_sliced: eigenvalues per slice the automatic edges aim at (default 1000) */
+  PFE_P_OVERLAP = 30        /* mixed precision: 1 (default) filters an iteration's FP32 and FP64 column groups
+                               concurrently, the FP32 group on a second stream of the context; 0: one after
+                               the other on the context's stream */
 };
 
 /* ---------------------------------------------------------------------------------------
@@ -305,13 +308,15 @@ pfe_status pfe_filter_apply_noalloc(pfe_ctx *ctx, int32_t m, const double *coeff
  * Machine measurement (no counterpart in the paper)
  * ------------------------------------------------------------------------------------- */
 
-/* The FP64 FMA throughput this GPU sustains, the ceiling of every FP64 step of the method (the
- * filter step on GB300 is bound by the FP64 pipe).  Launches, on `stream` (a cudaStream_t, NULL =
- * the legacy default stream), a kernel in which 8 CTAs of 256 threads per SM each advance 8
- * independent FMA chains `iters` times; the first launch warms up, the next `reps` are timed with
- * CUDA events on that stream.  *tflops receives 2 x FMAs / seconds / 1e12.  `sink` is one device
- * double the kernel writes only if a chain ends at a value it cannot reach (it keeps the chains
- * from being optimised away).  PFE_E_ARG for iters < 1, reps < 1, NULL sink or tflops. */
+/* The FP64 throughput this GPU sustains, the ceiling of every FP64 step of the method (the filter
+ * step on GB300 is bound by the FP64 pipe).  Launches, on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream), kernels in which every thread advances 8 or 16 independent chains `iters`
+ * times, with 4 or 8 CTAs of 256 threads per SM, either FMAs only or FMAs alternating with multiplies
+ * (the mix of the filter step); for each shape the first launch warms up and the next `reps` are
+ * timed with CUDA events on that stream.  *tflops receives the best rate, counting 2 flops per FP64
+ * instruction (the convention of the filter step's flop count).  `sink` is one device double the kernels write only if a chain ends at a value
+ * it cannot reach (it keeps the chains from being optimised away).  PFE_E_ARG for iters < 1,
+ * reps < 1, NULL sink or tflops. */
 pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stream, double *sink, double *tflops);
 
 /* ---------------------------------------------------------------------------------------

@@ -139,6 +139,10 @@ struct BatchDesc {
   const int32_t *rp;
   const int32_t *ci;
   const double *vals;  // filter operator A = (2/d)(H - cI)
+  // its rank-1 form when the sample has one (u null otherwise): pattern without diagonal blocks,
+  // 3 values per off-diagonal block, the symmetric diagonal blocks as (xx, xy, xz, yy, yz, zz)
+  const int32_t *rp1, *ci1;
+  const double *u, *dg;
   const double *X;
   double *b0, *b1, *Y;
   const double *coef;  // m + 1 damped coefficients
@@ -215,6 +219,10 @@ struct SolveState {
 struct pfe_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // mixed precision: the FP32 column group of an iteration runs on `side` while the FP64 group runs on
+  // `stream` (fork and join by events); created by the first mixed-precision solve
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
   int32_t N = 0;
@@ -249,6 +257,7 @@ struct pfe_ctx {
   int p_count_damping = 0;
   int32_t p_min_width = 16;
   double p_refine_tol = 1e-4;
+  int p_overlap = 1;
   int p_method = 0;
   int32_t p_block = 64;
   double p_basis_factor = 2.0;

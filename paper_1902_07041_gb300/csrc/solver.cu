@@ -489,6 +489,11 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   st.resid2 = red + colreduce_work(n, q);
   st.idx = idx;
   st.info = info;
+  if (st.fp32 && !ctx->side) {
+    PFE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    PFE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    PFE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
   if (st.fp32) {
     RESERVE(float, x32, ctx->w_f32a, big);
     RESERVE(float, y32, ctx->w_f32b, big);
@@ -530,22 +535,35 @@ pfe_status solve_filter(pfe_ctx *ctx) {
   const int32_t k64 = st.fp32 ? std::min(st.k64, st.act) : st.act;
   const int32_t k32 = st.act - k64;
   st.was64 = k32 == 0;
+  // Both groups present: the FP32 group (bound by memory latency and bandwidth) runs on the side
+  // stream concurrently with the FP64 group (bound by the FP64 pipe).  They touch disjoint columns:
+  // the FP64 group is a multiple of 4 columns, so its vector lanes end before column k64.
+  const bool split = k64 > 0 && k32 > 0 && ctx->p_overlap && ctx->side;
+  cudaStream_t s32 = split ? ctx->side : s;
+  if (split) {
+    PFE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, s));
+    PFE_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  if (k32 > 0) {
+    cudaEventRecord(st.ev32[0], s32);
+    st.f_launch += m1;
+    st.f_cols32 += (int64_t)k32 * m1;
+    launch_convert<double, float>(n, k32, st.X + k64, ld, st.X32 + k64, ld, s32);
+    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, k32, ld, st.X32 + k64, st.Y32 + k64,
+                              st.B32a + k64, st.B32b + k64, s32));
+    launch_convert<float, double>(n, k32, st.Y32 + k64, ld, st.Y + k64, ld, s32);
+    cudaEventRecord(st.ev32[1], s32);
+    st.timed32 = true;
+  }
   if (k64 > 0) {
     st.f_launch += m1;
     st.f_cols64 += (int64_t)k64 * m1;
     PFE_TRY(run_filter<double>(ctx, bsr_Hs64(ctx), ctx->coef.data(), ctx->m, k64, ld, st.X, st.Y, st.T0, st.T1, s));
     ++st.fp64_sweeps;
   }
-  if (k32 > 0) {
-    cudaEventRecord(st.ev32[0], s);
-    st.f_launch += m1;
-    st.f_cols32 += (int64_t)k32 * m1;
-    launch_convert<double, float>(n, k32, st.X + k64, ld, st.X32 + k64, ld, s);
-    PFE_TRY(run_filter<float>(ctx, bsr_Hs32(ctx), ctx->coef.data(), ctx->m, k32, ld, st.X32 + k64, st.Y32 + k64,
-                              st.B32a + k64, st.B32b + k64, s));
-    launch_convert<float, double>(n, k32, st.Y32 + k64, ld, st.Y + k64, ld, s);
-    cudaEventRecord(st.ev32[1], s);
-    st.timed32 = true;
+  if (split) {
+    PFE_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    PFE_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
   }
   st.matvecs += (int64_t)st.act * ctx->m;
   return PFE_OK;
@@ -807,6 +825,11 @@ int64_t batch_refresh(pfe_ctx **ctxs, int32_t ns, const std::vector<pfe_status> 
     d.rp = c->rp.as<int32_t>();
     d.ci = c->ci.as<int32_t>();
     d.vals = c->Hs64.as<double>();
+    const bool r1 = c->p_rank1 && c->r1_state == 1;
+    d.rp1 = r1 ? c->r1_rp.as<int32_t>() : nullptr;
+    d.ci1 = r1 ? c->r1_ci.as<int32_t>() : nullptr;
+    d.u = r1 ? c->r1_u64.as<double>() : nullptr;
+    d.dg = r1 ? c->r1_dg64.as<double>() : nullptr;
     d.X = st.X;
     d.b0 = st.T0;
     d.b1 = st.T1;
@@ -1155,6 +1178,12 @@ void pfe_destroy(pfe_ctx *ctx) {
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
   for (int e = 0; e < 2; ++e)
     if (ctx->solve.ev32[e]) cudaEventDestroy(ctx->solve.ev32[e]);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   delete ctx;
@@ -1285,6 +1314,10 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!int_ok(1)) return pfe_fail(ctx, PFE_E_ARG, "SLICE_TARGET must be an integer >= 1");
       ctx->p_slice_target = (int32_t)v;
       break;
+    case PFE_P_OVERLAP:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "OVERLAP must be 0 or 1");
+      ctx->p_overlap = (int)v;
+      break;
     case PFE_P_RANK1:
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "RANK1 must be 0 or 1");
       ctx->p_rank1 = (int)v;
@@ -1332,6 +1365,7 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_PHI: *v = ctx->p_phi; break;
     case PFE_P_DIRAC_CUT: *v = ctx->p_dirac_cut; break;
     case PFE_P_SLICE_TARGET: *v = ctx->p_slice_target; break;
+    case PFE_P_OVERLAP: *v = ctx->p_overlap; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;

@@ -35,6 +35,10 @@ def main():
     ap.add_argument("--sliced", type=int, default=0, help="spectrum slicing with this many eigenvalues a slice")
     ap.add_argument("--rate", type=float, default=0.1 ** 0.5, help="r of eq. (thresh) (piecewise quadratic filter)")
     ap.add_argument("--phi", type=float, default=0.8, help="phi of the Dirac filter")
+    ap.add_argument("--degree", type=int, default=0, help="filter degree (0: chosen by eq. (thresh))")
+    ap.add_argument("--width", type=int, default=0, help="subspace width (0: automatic)")
+    ap.add_argument("--overlap", type=int, default=1, help="mixed precision: FP32 and FP64 groups on two streams")
+    ap.add_argument("--refine-tol", type=float, default=1e-4, help="mixed precision: hand-over residual to FP64")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
@@ -44,7 +48,8 @@ def main():
         try:
             for key, v in (("PRECISION", a.precision), ("METHOD", a.method), ("BLOCK", a.block),
                            ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1), ("FILTER", a.filter),
-                           ("DAMPING", a.damping), ("RATE", a.rate), ("PHI", a.phi)):
+                           ("DAMPING", a.damping), ("RATE", a.rate), ("PHI", a.phi), ("DEGREE", a.degree),
+                           ("WIDTH", a.width), ("OVERLAP", a.overlap), ("REFINE_TOL", a.refine_tol)):
                 pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), v)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -61,7 +66,8 @@ def main():
             print(json.dumps({"n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi, "method": a.method,
                               "precision": a.precision, "block": a.block, "basis_factor": a.basis_factor,
                               "filter": a.filter, "damping": a.damping, "sliced": a.sliced, "rate": a.rate,
-                              "phi": a.phi,
+                              "phi": a.phi, "degree_set": a.degree, "width_set": a.width, "overlap": a.overlap,
+                              "refine_tol": a.refine_tol,
                               "rank1_in_use": pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1), "wall_s": wall,
                               "status": st, **stats}), flush=True)
         finally:

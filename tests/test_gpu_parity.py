@@ -321,8 +321,10 @@ def test_solve_config_n1000_degree40():
     _solve_and_check(glassgen.generate(1000, 0), 0.02, 0.05, DEGREE=40, WIDTH=256, MAX_ITERS=200)
 
 
-def test_solve_mixed_precision_matches_fp64_accuracy():
-    st = _solve_and_check(glassgen.generate(300, 5), 0.05, 0.12, precision=1)
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_solve_mixed_precision_matches_fp64_accuracy(overlap):
+    """Mixed precision, with the FP32 and FP64 column groups on two streams (1) or on one (0)."""
+    st = _solve_and_check(glassgen.generate(300, 5), 0.05, 0.12, precision=1, OVERLAP=overlap)
     assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] > 0  # both precisions were used
 
 
