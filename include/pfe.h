@@ -70,7 +70,10 @@ enum {
   PFE_P_WIDTH_FACTOR = 6,   /* default 1.5 */
   PFE_P_TOL = 7,            /* residual tolerance ||H v - lambda v|| / lambda_max_est (default 1e-8) */
   PFE_P_PRECISION = 8,      /* filter precision: 0 FP64 (default); 1 mixed: each Ritz pair is filtered in
-                               FP32 while its residual exceeds REFINE_TOL, in FP64 after */
+                               FP32 while its residual exceeds REFINE_TOL, in FP64 after; 2 mixed by defect
+                               correction: as 1, but below REFINE_TOL the pair's filter is split exactly into
+                               x p(theta) in FP64 plus a recurrence on its residual H x - theta x in FP32 (no
+                               FP64 filter sweep); the dense steps and residuals are FP64 in every mode */
   PFE_P_MAX_ITERS = 9,      /* subspace-iteration limit (default 60) */
   PFE_P_SEED = 10,          /* seed of the random start block and estimator vectors (default 0) */
   PFE_P_LAMBDA_MAX = 11,    /* spectrum upper bound; 0 = estimate by Lanczos (default 0) */
@@ -110,9 +113,16 @@ enum {
   PFE_P_DIRAC_CUT = 28,     /* Dirac filter with METHOD 1: Ritz values of rho(Ht) >= DIRAC_CUT x rho(xi) are
                                wanted (default 0.9) */
   PFE_P_SLICE_TARGET = 29,  /* pfe_solve_sliced: eigenvalues per slice the automatic edges aim at (default 1000) */
-  PFE_P_OVERLAP = 30        /* mixed precision: 1 (default) filters an iteration's FP32 and FP64 column groups
-                               concurrently, the FP32 group on a second stream of the context; 0: one after
-                               the other on the context's stream */
+  PFE_P_OVERLAP = 30,       /* PRECISION 1: 1 filters an iteration's FP32 and FP64 column groups concurrently,
+                               the FP32 group on a second stream of the context; 0 (default): one after the
+                               other on the context's stream */
+  PFE_P_DEGREE_RULE = 31    /* subspace iteration with the automatic degree (DEGREE 0, RATE not set):
+                               1 (default) raises the degree of eq. (thresh) at r = sqrt(0.1) to the one in
+                               [m, 4m] that minimises a model of the solve's work once the width is known
+                               (iterations from the filter's largest value outside the margin window over its
+                               smallest value in [a, b], times the filter and dense work of one); 0 keeps the
+                               degree of eq. (thresh).  pfe_get_filter reports the degree in use (after a
+                               solve, the one the solve used) */
 };
 
 /* ---------------------------------------------------------------------------------------

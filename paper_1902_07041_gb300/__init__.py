@@ -35,6 +35,7 @@ PFE_P_LANCZOS_STEPS, PFE_P_COUNT_DAMPING, PFE_P_MIN_WIDTH, PFE_P_REFINE_TOL = 15
 PFE_P_STEP_SHAPE_F64, PFE_P_STEP_SHAPE_F32 = 19, 20
 PFE_P_METHOD, PFE_P_BLOCK, PFE_P_BASIS_FACTOR, PFE_P_BATCH_THREADS, PFE_P_RANK1 = 21, 22, 23, 24, 25
 PFE_P_FILTER, PFE_P_PHI, PFE_P_DIRAC_CUT, PFE_P_SLICE_TARGET, PFE_P_OVERLAP = 26, 27, 28, 29, 30
+PFE_P_DEGREE_RULE = 31
 
 # every entry point declared in include/pfe.h
 EXPORTS = ("pfe_springs_to_bsr", "pfe_create", "pfe_destroy", "pfe_last_error", "pfe_set_param",

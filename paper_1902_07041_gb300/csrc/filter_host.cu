@@ -247,6 +247,51 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
   *last = z[n - 1];
 }
 
+// Largest |p(x)| outside the margin window [xi - eps, eta + eps] over the smallest p(x) in [xi, eta],
+// for p = sum c_j T_j: the factor by which one filter application shrinks the components a subspace
+// holding the window does not capture (eq. (thresh) bounds it at the two margin points only).  The
+// outside is sampled in theta = arccos x with a step of pi / (6 m), fine enough for the oscillations
+// of a degree-m series; the inside at 65 points including both edges.
+double filter_ratio(const std::vector<double> &c, int32_t m, double xi, double eta, double eps) {
+  const double kPi = 3.14159265358979323846;
+  const double lo = std::max(-1.0, xi - eps), hi = std::min(1.0, eta + eps);
+  double out = 0.0;
+  const double h = kPi / (6.0 * std::max(m, 1));
+  const double th_hi = std::acos(hi), th_lo = std::acos(lo);  // x in [hi, 1] <-> theta in [0, th_hi]
+  for (double th = 0.0; th <= th_hi; th += h) out = std::max(out, std::fabs(chebyshev_value(c, m, std::cos(th))));
+  if (hi < 1.0) out = std::max(out, std::fabs(chebyshev_value(c, m, hi)));
+  for (double th = th_lo; th <= kPi; th += h) out = std::max(out, std::fabs(chebyshev_value(c, m, std::cos(th))));
+  if (lo > -1.0) out = std::max(out, std::fabs(chebyshev_value(c, m, lo)));
+  double in = 1e300;
+  for (int i = 0; i <= 64; ++i) in = std::min(in, chebyshev_value(c, m, xi + (eta - xi) * i / 64.0));
+  return in > 0.0 ? out / in : 1e300;
+}
+
+// The degree in [m0, 4 m0] (steps of 5 %) that minimises the modelled work of the subspace iteration:
+// iterations log(tol) / log(ratio(m)) times the work of one, m filter steps plus the dense steps, the
+// latter as dense_steps equivalent filter steps (work of CholQR2, Rayleigh-Ritz and locking over the
+// work of one filter step on the block).  m0 when no candidate beats it.
+int32_t choose_degree_cost(double xi, double eta, double eps, int kind, int32_t m0, double tol, double dense_steps) {
+  if (m0 < 1 || !(tol > 0.0 && tol < 1.0)) return m0;
+  int32_t best = m0;
+  double best_cost = 1e300;
+  std::vector<double> gam, g, c;
+  for (int32_t m = m0; m <= 4 * m0 && m <= 60000; m = std::max(m + 1, (int32_t)std::lround(m * 1.05))) {
+    pq_coefficients(xi, eta, eps, m, gam);
+    damping_factors(kind, m, g);
+    c.resize((size_t)m + 1);
+    for (int32_t j = 0; j <= m; ++j) c[j] = gam[j] * g[j];
+    const double r = filter_ratio(c, m, xi, eta, eps);
+    if (!(r > 0.0 && r < 1.0)) continue;
+    const double cost = std::log(tol) / std::log(r) * ((double)m + dense_steps);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = m;
+    }
+  }
+  return best;
+}
+
 }  // namespace pfe
 
 // ---- the filter design without a context (host only, callable without a GPU)

@@ -153,6 +153,19 @@ struct BatchDesc {
 void launch_batch_step(int cpl, int blocks, const BatchDesc *desc, int32_t nsamp, const int64_t *total, int32_t step,
                        cudaStream_t s);
 
+// Mixed-precision filter by defect correction (defect.cu).  Step with forcing, FP32:
+//   Z = A X - W + fs[c] F;  MODE_STEP: Y += g1 Z (Y may be null);  MODE_STEP_ACC: Y += g0 X + g1 Z
+void launch_defect_step(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W, float *Z,
+                        float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s);
+// start of a block whose first kd of act columns are defect columns (Rt = (W - theta X) inv_d):
+//   defect: X32 = 0, B = Rt, F = Rt, Y32 = g1 Rt;  plain: X32 = X, F = 0
+void launch_defect_prep(int64_t n, int32_t act, int32_t kd, const double *X, const double *W, int64_t ld,
+                        const double *theta, double inv_d, double g1, float *X32, float *B, float *F, float *Y32,
+                        cudaStream_t s);
+// Y = pth[c] X + Y32 over act columns
+void launch_defect_combine(int64_t n, int32_t act, const double *X, int64_t ld, const double *pth, const float *Y32,
+                           double *Y, cudaStream_t s);
+
 // --------------------------------------------------------------------------------------
 // FP64 tensor-core (DMMA) products
 // --------------------------------------------------------------------------------------
@@ -182,6 +195,10 @@ void damping_factors(int kind, int32_t m, std::vector<double> &g);
 double chebyshev_value(const std::vector<double> &c, int32_t m, double x);
 // smallest degree satisfying eq. (thresh), or -1
 int32_t choose_degree(double xi, double eta, double eps, double r, int kind, int32_t kmax);
+// largest |p| outside the margin window over the smallest p inside [xi, eta] (sampled)
+double filter_ratio(const std::vector<double> &c, int32_t m, double xi, double eta, double eps);
+// degree in [m0, 4 m0] minimising log(tol) / log(filter_ratio(m)) x (m + dense_steps)
+int32_t choose_degree_cost(double xi, double eta, double eps, int kind, int32_t m0, double tol, double dense_steps);
 // Dirac filter of eq. (cheby-delta.1): damped coefficients for centre gamma; the centre with equal
 // values at xi and eta; the smallest degree whose balanced filter has rho(xi) / rho(gamma) <= phi
 void dirac_coefficients(double gamma, int32_t m, int kind, std::vector<double> &c);
@@ -198,6 +215,13 @@ void tridiag_top(const std::vector<double> &alpha, const std::vector<double> &be
 struct SolveState {
   bool fp32 = false, use64 = true, was64 = true, done = false, timed_filter = true, timed32 = false;
   bool active = false;  // a stepwise solve (pfe_solve_begin .. pfe_solve_end) is in progress
+  // PRECISION 2: the hand-over group is filtered in FP32 by defect correction (defect.cu) instead of FP64
+  bool defect = false;
+  std::vector<double> theta_act;     // Ritz values of the active columns, in their current order
+  std::vector<double> h_pth;         // p(theta_t) per active column (0 for plain FP32 columns)
+  std::vector<float> h_fs;           // 2 T_j(theta_t) per step j and column (row-major m x ld)
+  float *R32 = nullptr, *dfs = nullptr;
+  double *dtheta = nullptr, *dpth = nullptr;
   int32_t q = 0, act = 0, nl = 0, it = 0, prev_count = -1, fp64_sweeps = 0;
   int32_t k64 = 0;  // mixed precision: the first k64 active columns use the FP64 filter
   int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
@@ -257,7 +281,8 @@ struct pfe_ctx {
   int p_count_damping = 0;
   int32_t p_min_width = 16;
   double p_refine_tol = 1e-4;
-  int p_overlap = 1;
+  int p_overlap = 0;
+  int p_degree_rule = 1;
   int p_method = 0;
   int32_t p_block = 64;
   double p_basis_factor = 2.0;
@@ -276,6 +301,7 @@ struct pfe_ctx {
   double count_est = 0;
   bool has_filter = false;
   int32_t m = 0;
+  int32_t m_thresh = 0;  // the degree of eq. (thresh) before any raise by the cost model
   std::vector<double> coef;
   double tc = 0, td = 0, xi = 0, eta = 0, eps = 0;
   double dirac_gamma = 0, dirac_tau = 0;  // Dirac filter: centre and the (equal) value at xi and eta
@@ -292,7 +318,7 @@ struct pfe_ctx {
 
   // workspaces
   pfe::DBuf w_X, w_Y, w_W, w_T0, w_T1, w_T2, w_small, w_small2, w_red, w_idx, w_cs_work, w_info, w_f32a, w_f32b,
-      w_f32c, w_f32d, w_ckpt, w_rr, w_gram, w_bks[5], w_slice[2];
+      w_f32c, w_f32d, w_ckpt, w_rr, w_gram, w_bks[5], w_slice[2], w_f32e, w_defect, w_tau;
   int64_t launch_base = 0;  // process-wide launch counter when the context was created
   SolveState solve;
   pfe::DBuf dcoef;            // filter coefficients on the device (batched solves)

@@ -10,26 +10,24 @@ namespace {
 // FMA; MIX = 1: FMA chains and multiply chains alternate (the instruction mix of the filter step,
 // whose dot products start with a multiply).  Rates count 2 flops per FP64 instruction, the
 // convention of the filter's own flop count (each FMA, and each multiply that starts a dot product).
+// MIX = 2: FMAs whose multiplier and addend differ per chain (no operand shared between chains).
 template <int CHAINS, int MIX>
 __global__ void __launch_bounds__(256) k_fp64_probe(int32_t iters, double *sink) {
-  double a[CHAINS];
-  const double b = 1.0 - 1e-12 * (double)(threadIdx.x & 7);
-  const double c = 1e-9;
+  double a[CHAINS], b[CHAINS], c[CHAINS];
 #pragma unroll
-  for (int i = 0; i < CHAINS; ++i) a[i] = (double)(threadIdx.x + i) * 1e-3 + 0.5;
+  for (int i = 0; i < CHAINS; ++i) {
+    a[i] = (double)(threadIdx.x + i) * 1e-3 + 0.5;
+    b[i] = 1.0 - 1e-12 * (double)((threadIdx.x + (MIX == 2 ? i : 0)) & 7);
+    c[i] = 1e-9 * (MIX == 2 ? (double)(i + 1) : 1.0);
+  }
   for (int32_t t = 0; t < iters; ++t) {
 #pragma unroll
-    for (int i = 0; i < CHAINS; ++i) a[i] = (MIX == 1 && (i & 1)) ? a[i] * b : fma(a[i], b, c);
+    for (int i = 0; i < CHAINS; ++i) a[i] = (MIX == 1 && (i & 1)) ? a[i] * b[i] : fma(a[i], b[i], c[i]);
   }
   double s = 0.0;
 #pragma unroll
   for (int i = 0; i < CHAINS; ++i) s += a[i];
   if (s == -1.0) *sink = s;  // never true (every chain stays positive); the store keeps the work live
-}
-
-template <int CHAINS, int MIX>
-double flops_per_thread(int32_t iters) {
-  return 2.0 * CHAINS * (double)iters;  // 2 per FP64 instruction
 }
 
 }  // namespace
@@ -51,11 +49,12 @@ extern "C" pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stre
   double best = 0.0;
   cudaError_t err = cudaSuccess;
   // shapes: {chains, mix, CTAs per SM}
-  const int shapes[][3] = {{8, 0, 8}, {16, 0, 8}, {8, 0, 4}, {16, 0, 4}, {8, 1, 8}, {16, 1, 8}};
+  const int shapes[][3] = {{8, 0, 8}, {16, 0, 8}, {8, 0, 4}, {16, 0, 4}, {8, 1, 8}, {16, 1, 8}, {8, 2, 8}, {8, 2, 4}};
   for (const auto &sh : shapes) {
     const unsigned blocks = (unsigned)sms * (unsigned)sh[2];
     auto launch = [&]() {
-      if (sh[0] == 8 && sh[1] == 0) PFE_LAUNCH k_fp64_probe<8, 0><<<blocks, 256, 0, s>>>(iters, sink);
+      if (sh[1] == 2) PFE_LAUNCH k_fp64_probe<8, 2><<<blocks, 256, 0, s>>>(iters, sink);
+      else if (sh[0] == 8 && sh[1] == 0) PFE_LAUNCH k_fp64_probe<8, 0><<<blocks, 256, 0, s>>>(iters, sink);
       else if (sh[0] == 16 && sh[1] == 0) PFE_LAUNCH k_fp64_probe<16, 0><<<blocks, 256, 0, s>>>(iters, sink);
       else if (sh[0] == 8) PFE_LAUNCH k_fp64_probe<8, 1><<<blocks, 256, 0, s>>>(iters, sink);
       else PFE_LAUNCH k_fp64_probe<16, 1><<<blocks, 256, 0, s>>>(iters, sink);
@@ -69,8 +68,7 @@ extern "C" pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stre
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err != cudaSuccess || ms <= 0.f) break;
-    const double fpt = sh[0] == 8 ? (sh[1] ? flops_per_thread<8, 1>(iters) : flops_per_thread<8, 0>(iters))
-                                  : (sh[1] ? flops_per_thread<16, 1>(iters) : flops_per_thread<16, 0>(iters));
+    const double fpt = 2.0 * sh[0] * (double)iters;  // 2 per FP64 instruction
     const double rate = fpt * (double)blocks * 256.0 * (double)reps / (ms * 1e-3) / 1e12;
     best = rate > best ? rate : best;
   }

@@ -246,6 +246,16 @@ pfe_status ensure_hs(pfe_ctx *ctx, bool need32) {
   return PFE_OK;
 }
 
+// damped coefficients of the piecewise quadratic filter of degree m (App. A, Sec. 2.3) into the context
+void set_pq_filter(pfe_ctx *ctx, int32_t m) {
+  std::vector<double> gam, g;
+  pq_coefficients(ctx->xi, ctx->eta, ctx->eps, m, gam);
+  damping_factors(ctx->p_damping, m, g);
+  ctx->coef.resize((size_t)m + 1);
+  for (int32_t j = 0; j <= m; ++j) ctx->coef[j] = gam[j] * g[j];
+  ctx->m = m;
+}
+
 pfe_status ensure_filter(pfe_ctx *ctx) {
   if (ctx->has_filter) return PFE_OK;
   if (!ctx->has_interval) return pfe_fail(ctx, PFE_E_STATE, "no interval set (pfe_set_interval)");
@@ -270,13 +280,27 @@ pfe_status ensure_filter(pfe_ctx *ctx) {
     m = choose_degree(ctx->xi, ctx->eta, ctx->eps, ctx->rate_of(), ctx->p_damping, 60000);
     if (m < 0) return pfe_fail(ctx, PFE_E_ARG, "no filter degree <= 60000 meets the rate; widen eps or r");
   }
-  std::vector<double> gam, g;
-  pq_coefficients(ctx->xi, ctx->eta, ctx->eps, m, gam);
-  damping_factors(ctx->p_damping, m, g);
-  ctx->coef.resize((size_t)m + 1);
-  for (int32_t j = 0; j <= m; ++j) ctx->coef[j] = gam[j] * g[j];
-  ctx->m = m;
+  ctx->m_thresh = m;
+  set_pq_filter(ctx, m);
   ctx->has_filter = true;
+  return PFE_OK;
+}
+
+// The subspace iteration's automatic degree (no DEGREE, no RATE set, DEGREE_RULE 1): raised from the
+// degree of eq. (thresh) at r = sqrt(0.1) to the one that minimises a model of the solve's work once the
+// width q is known.  One filter step costs F per column (flops of the rank-1 or full-block operator);
+// the dense steps of an iteration (Gram matrices and block updates of CholQR2, Rayleigh-Ritz and the
+// projection) about 5.5 n q^2 flops; FP32 filter steps (mixed precision) are memory bound and cost
+// about a tenth of an FP64 step (a half with the per-pair FP64 hand-over of PRECISION 1).
+pfe_status apply_degree_rule(pfe_ctx *ctx, int32_t q) {
+  if (ctx->p_degree_rule != 1 || ctx->p_degree > 0 || ctx->p_rate > 0.0 || ctx->p_filter != 0) return PFE_OK;
+  const double n = (double)ctx->n, N = (double)ctx->N, nnzb = (double)ctx->nnzb;
+  const bool r1 = ctx->p_rank1 && ctx->r1_state == 1;
+  const double F = r1 ? 12.0 * (nnzb - N) + 18.0 * N + 6.0 * n : 18.0 * nnzb + 6.0 * n;
+  const double rel = ctx->p_precision == 0 ? 1.0 : (ctx->p_precision == 1 ? 0.5 : 0.1);
+  const double dense_steps = 5.5 * n * (double)q / F / rel;
+  const int32_t m = choose_degree_cost(ctx->xi, ctx->eta, ctx->eps, ctx->p_damping, ctx->m_thresh, ctx->p_tol, dense_steps);
+  if (m != ctx->m) set_pq_filter(ctx, m);
   return PFE_OK;
 }
 
@@ -453,7 +477,8 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   ctx->n_found = 0;
   ctx->stats = pfe_stats{};
   ctx->shift_count = 0;
-  st.fp32 = ctx->p_precision == 1;
+  st.fp32 = ctx->p_precision >= 1;
+  st.defect = ctx->p_precision == 2;
   PFE_TRY(ensure_filter(ctx));
   PFE_TRY(ensure_hs(ctx, st.fp32));
   int32_t q = ctx->p_width;
@@ -466,6 +491,7 @@ pfe_status solve_setup(pfe_ctx *ctx) {
     q = std::max(q, ctx->p_min_width);
   }
   q = (int32_t)std::min<int64_t>(q, ctx->n);
+  PFE_TRY(apply_degree_rule(ctx, q));
   const int64_t n = ctx->n, ld = round_up(q, 4);
   st.q = q;
   st.ld = ld;
@@ -501,6 +527,16 @@ pfe_status solve_setup(pfe_ctx *ctx) {
     RESERVE(float, b32, ctx->w_f32d, big);
     st.X32 = x32; st.Y32 = y32; st.B32a = a32; st.B32b = b32;
     for (float *p : {x32, y32, a32, b32}) launch_zero<float>(p, (int64_t)big, s);
+    if (st.defect) {
+      RESERVE(float, r32, ctx->w_f32e, big);
+      RESERVE(double, dd, ctx->w_defect, 2 * (size_t)ld + 8);
+      RESERVE(float, tau, ctx->w_tau, (size_t)std::max(ctx->m, 1) * ld);
+      launch_zero<float>(r32, (int64_t)big, s);
+      st.R32 = r32;
+      st.dtheta = dd;
+      st.dpth = dd + ld;
+      st.dfs = tau;
+    }
   }
   for (double *p : {X, Y, W, T0, T1, L}) launch_zero<double>(p, (int64_t)big, s);
   for (int e = 0; e < 4; ++e)
@@ -524,6 +560,65 @@ pfe_status solve_setup(pfe_ctx *ctx) {
   return PFE_OK;
 }
 
+// PRECISION 2: the first kd active columns (residual below the hand-over tolerance) are filtered by
+// defect correction, the others by the plain FP32 recurrence, all in one FP32 launch per step:
+//   prep (Rt = (W - X Theta)/d for the defect columns; X rounded for the plain ones), the first step of
+//   the plain columns, steps 1 .. m-1 with the forcing 2 T_j(theta_t) Rt, then Y = X p(Theta_t) + Y32.
+pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
+  SolveState &st = ctx->solve;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->n, ld = st.ld;
+  const int32_t act = st.act, m = ctx->m, kp = act - kd;
+  const std::vector<double> &g = ctx->coef;
+  if (m < 1) {  // degree 0: y = g0 x
+    launch_axpby<double>(n, act, g[0], st.X, ld, 0.0, st.Y, ld, s);
+    return check_launch(ctx, "filter (degree 0)");
+  }
+  if ((int32_t)st.theta_act.size() < kd) return pfe_fail(ctx, PFE_E_STATE, "defect filter without Ritz values");
+  // host: theta_t, the Chebyshev values T_j(theta_t) (three-term recurrence), p(theta_t)
+  st.h_pth.assign((size_t)act, 0.0);
+  st.h_fs.assign((size_t)m * ld, 0.f);
+  for (int32_t c = 0; c < kd; ++c) {
+    const double tt = (st.theta_act[c] - ctx->tc) / ctx->td;
+    double tm = 1.0, tj = tt, p = g[0] + g[1] * tt;
+    for (int32_t j = 1; j < m; ++j) {
+      st.h_fs[(size_t)j * ld + c] = (float)(2.0 * tj);
+      const double tn = 2.0 * tt * tj - tm;
+      tm = tj;
+      tj = tn;
+      p += g[j + 1] * tj;
+    }
+    st.h_pth[c] = p;
+  }
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.dtheta, st.theta_act.data(), sizeof(double) * kd, cudaMemcpyHostToDevice, s));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.dpth, st.h_pth.data(), sizeof(double) * act, cudaMemcpyHostToDevice, s));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.dfs, st.h_fs.data(), sizeof(float) * st.h_fs.size(), cudaMemcpyHostToDevice, s));
+  cudaEventRecord(st.ev32[0], s);
+  const Bsr<float> A = bsr_Hs32(ctx);
+  launch_defect_prep(n, act, kd, st.X, st.W, ld, st.dtheta, 1.0 / ctx->td, g[1], st.X32, st.B32a, st.R32, st.Y32, s);
+  if (kp > 0)  // t_1 = A t_0 / 2 and y = g0 t_0 + g1 t_1 for the plain columns
+    launch_bsr_step<float>(A, MODE_FIRST, kp, ld, st.X32 + kd, nullptr, st.B32a + kd, st.Y32 + kd, 0.5f, 0.f,
+                           (float)g[0], (float)g[1], s);
+  const float *tprev = st.X32;
+  float *tcur = st.B32a;
+  for (int32_t j = 1; j < m; ++j) {
+    float *out = (tprev == st.X32) ? st.B32b : const_cast<float *>(tprev);
+    const bool even = (j % 2) == 0, last = j == m - 1;
+    launch_defect_step(A, even ? MODE_STEP_ACC : MODE_STEP, act, ld, tcur, tprev, out, (even || last) ? st.Y32 : nullptr,
+                       st.R32, st.dfs + (size_t)j * ld, (float)g[j], (float)g[j + 1], s);
+    tprev = tcur;
+    tcur = out;
+  }
+  launch_defect_combine(n, act, st.X, ld, st.dpth, st.Y32, st.Y, s);
+  cudaEventRecord(st.ev32[1], s);
+  st.timed32 = true;
+  st.was64 = false;
+  st.f_launch += m;
+  st.f_cols32 += (int64_t)act * m;
+  st.matvecs += (int64_t)act * m;
+  return check_launch(ctx, "defect-corrected filter");
+}
+
 // Y = p(Ht) X on the active columns (the single-context path).  In the mixed-precision mode the
 // active block is ordered [FP64 columns | FP32 columns]: pairs whose residual is already below the
 // hand-over tolerance are filtered in FP64, the others in FP32 (st.k64 columns in FP64).
@@ -538,6 +633,7 @@ pfe_status solve_filter(pfe_ctx *ctx) {
   // Both groups present: the FP32 group (bound by memory latency and bandwidth) runs on the side
   // stream concurrently with the FP64 group (bound by the FP64 pipe).  They touch disjoint columns:
   // the FP64 group is a multiple of 4 columns, so its vector lanes end before column k64.
+  if (st.defect && k64 > 0) return solve_filter_defect(ctx, k64);
   const bool split = k64 > 0 && k32 > 0 && ctx->p_overlap && ctx->side;
   cudaStream_t s32 = split ? ctx->side : s;
   if (split) {
@@ -687,9 +783,20 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
                                         cudaMemcpyHostToDevice, s));
       launch_gather_cols(n, (int32_t)keep_cols.size(), st.X, ld, st.Y, ld, st.idx, s);
       std::swap(st.X, st.Y);
+      if (st.defect) {  // W = H X follows the kept columns (the next defect filter reads it)
+        launch_gather_cols(n, (int32_t)keep_cols.size(), st.W, ld, st.T0, ld, st.idx, s);
+        std::swap(st.W, st.T0);
+      }
     }
     PFE_TRY(check_launch(ctx, "locking"));
     PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // the host index vectors must outlive the copies
+  }
+  if (st.defect) {
+    st.theta_act.clear();
+    if (!lock_cols.empty() || reorder)
+      for (int32_t j : keep_cols) st.theta_act.push_back(st.hth[j]);
+    else
+      st.theta_act.assign(st.hth.begin(), st.hth.begin() + act);
   }
   st.act = (int32_t)keep_cols.size();
   if ((unconv_in == 0 && count_in == st.prev_count && st.it >= 2) || st.act == 0) {
@@ -1229,7 +1336,7 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       ctx->p_tol = v;
       break;
     case PFE_P_PRECISION:
-      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "PRECISION must be 0 or 1");
+      if (!(v == 0 || v == 1 || v == 2)) return pfe_fail(ctx, PFE_E_ARG, "PRECISION must be 0, 1 or 2");
       ctx->p_precision = (int)v;
       break;
     case PFE_P_MAX_ITERS:
@@ -1318,6 +1425,11 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "OVERLAP must be 0 or 1");
       ctx->p_overlap = (int)v;
       break;
+    case PFE_P_DEGREE_RULE:
+      if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "DEGREE_RULE must be 0 or 1");
+      ctx->p_degree_rule = (int)v;
+      ctx->has_filter = false;
+      break;
     case PFE_P_RANK1:
       if (!(v == 0 || v == 1)) return pfe_fail(ctx, PFE_E_ARG, "RANK1 must be 0 or 1");
       ctx->p_rank1 = (int)v;
@@ -1366,6 +1478,7 @@ pfe_status pfe_get_param(const pfe_ctx *ctx, int key, double *v) {
     case PFE_P_DIRAC_CUT: *v = ctx->p_dirac_cut; break;
     case PFE_P_SLICE_TARGET: *v = ctx->p_slice_target; break;
     case PFE_P_OVERLAP: *v = ctx->p_overlap; break;
+    case PFE_P_DEGREE_RULE: *v = ctx->p_degree_rule; break;
     case PFE_P_STEP_SHAPE_F64: *v = step_variant(0); break;
     case PFE_P_STEP_SHAPE_F32: *v = step_variant(1); break;
     default: return PFE_E_ARG;

@@ -33,12 +33,14 @@ def main():
     ap.add_argument("--filter", type=int, default=0, help="0 piecewise quadratic, 1 Dirac (with --method 1)")
     ap.add_argument("--damping", type=int, default=0, help="0 none, 1 Jackson, 2 Lanczos")
     ap.add_argument("--sliced", type=int, default=0, help="spectrum slicing with this many eigenvalues a slice")
-    ap.add_argument("--rate", type=float, default=0.1 ** 0.5, help="r of eq. (thresh) (piecewise quadratic filter)")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="r of eq. (thresh) (piecewise quadratic filter); 0: the method's default and degree rule")
     ap.add_argument("--phi", type=float, default=0.8, help="phi of the Dirac filter")
     ap.add_argument("--degree", type=int, default=0, help="filter degree (0: chosen by eq. (thresh))")
     ap.add_argument("--width", type=int, default=0, help="subspace width (0: automatic)")
     ap.add_argument("--overlap", type=int, default=1, help="mixed precision: FP32 and FP64 groups on two streams")
     ap.add_argument("--refine-tol", type=float, default=1e-4, help="mixed precision: hand-over residual to FP64")
+    ap.add_argument("--degree-rule", type=int, default=1, help="1: cost-model degree (automatic degree only)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
@@ -48,9 +50,12 @@ def main():
         try:
             for key, v in (("PRECISION", a.precision), ("METHOD", a.method), ("BLOCK", a.block),
                            ("BASIS_FACTOR", a.basis_factor), ("RANK1", a.rank1), ("FILTER", a.filter),
-                           ("DAMPING", a.damping), ("RATE", a.rate), ("PHI", a.phi), ("DEGREE", a.degree),
-                           ("WIDTH", a.width), ("OVERLAP", a.overlap), ("REFINE_TOL", a.refine_tol)):
+                           ("DAMPING", a.damping), ("PHI", a.phi), ("DEGREE", a.degree),
+                           ("WIDTH", a.width), ("OVERLAP", a.overlap), ("REFINE_TOL", a.refine_tol),
+                           ("DEGREE_RULE", a.degree_rule)):
                 pfe.pfe_set_param(ctx, getattr(pfe, "PFE_P_" + key), v)
+            if a.rate > 0:
+                pfe.pfe_set_param(ctx, pfe.PFE_P_RATE, a.rate)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             lmax, _ = pfe.pfe_estimate(ctx)
@@ -67,7 +72,7 @@ def main():
                               "precision": a.precision, "block": a.block, "basis_factor": a.basis_factor,
                               "filter": a.filter, "damping": a.damping, "sliced": a.sliced, "rate": a.rate,
                               "phi": a.phi, "degree_set": a.degree, "width_set": a.width, "overlap": a.overlap,
-                              "refine_tol": a.refine_tol,
+                              "refine_tol": a.refine_tol, "degree_rule": a.degree_rule,
                               "rank1_in_use": pfe.pfe_get_param(ctx, pfe.PFE_P_RANK1), "wall_s": wall,
                               "status": st, **stats}), flush=True)
         finally:

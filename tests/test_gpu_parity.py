@@ -328,6 +328,16 @@ def test_solve_mixed_precision_matches_fp64_accuracy(overlap):
     assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] > 0  # both precisions were used
 
 
+@pytest.mark.parametrize("N,seed,lo,hi", [(300, 5, 0.05, 0.12), (1000, 0, 0.02, 0.05)])
+def test_solve_defect_corrected_fp32_filter_reaches_fp64_accuracy(N, seed, lo, hi):
+    """PRECISION 2: every filter application runs in FP32 (below the hand-over residual by defect
+    correction: x p(theta) in FP64 plus the recurrence on the residual in FP32).  The plain FP32 filter
+    alone stalls near its rounding level (~1e-4 of lambda_max); reaching the 1e-8 residuals, the exact
+    count and the 1e-10 eigenvalues with no FP64 filter sweep shows the correction at work."""
+    st = _solve_and_check(glassgen.generate(N, seed), lo, hi, precision=2)
+    assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] == 0 and st["fp64_sweeps"] == 0
+
+
 @pytest.mark.parametrize("block", [16, 64])
 def test_solve_block_lanczos(block):
     """Thick-restart block Lanczos on p(Ht) + Rayleigh-Ritz with H (PFE_P_METHOD = 1)."""
