@@ -254,6 +254,8 @@ typedef struct {
   int32_t locked;              /* stepwise solve in progress: converged pairs locked so far (0 otherwise) */
   int32_t cholqr_shifts;       /* Cholesky factorisations of CholQR2 that broke down and were repeated
                                   with the shift of the retry (numerically rank-deficient blocks) */
+  int64_t filter_col_steps_forced; /* PRECISION 2: the part of filter_col_steps_f32 run by the step with
+                                  the forcing term (it also reads the residual block) */
 } pfe_stats;
 /* Between pfe_solve_begin and pfe_solve_end the counters iterations, matvecs, width, degree,
  * active, locked and kernel_launches describe the solve in progress; the other fields are those of
@@ -340,9 +342,10 @@ pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stream, double 
  * grid size chosen by timing the candidates on the first call); the dense steps run per sample,
  * the samples' dense steps concurrently from PFE_P_BATCH_THREADS host threads.  When every context
  * selects PFE_P_METHOD = 1 the samples' block Lanczos solves run whole, concurrently from those
- * threads, each on its own stream; each sample releases its work buffers when its solve ends (its
- * eigenvectors stay), and a sample that ran out of device memory beside the others is solved again
- * afterwards, alone.  All contexts of a batch select the same method (PFE_E_ARG otherwise).
+ * threads, each on its own stream, largest samples first; a finished sample's work buffers pass to
+ * the next sample its thread solves (its eigenvectors stay), so only the solves in flight hold them
+ * and none is freed while others run, and a sample that ran out of device memory beside the others
+ * is solved again afterwards, alone.  All contexts of a batch select the same method (PFE_E_ARG otherwise).
  * In the stats of every sample seconds_filter is the batch's shared filter time.
  * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);

@@ -64,7 +64,8 @@ class PfeStats(ctypes.Structure):
                 ("seconds_filter_f32", ctypes.c_double), ("batch_replays", ctypes.c_int64),
                 ("restarts", ctypes.c_int32), ("basis", ctypes.c_int32), ("filter_shape_f64", ctypes.c_int32),
                 ("filter_shape_f32", ctypes.c_int32), ("slices", ctypes.c_int32), ("active", ctypes.c_int32),
-                ("locked", ctypes.c_int32), ("cholqr_shifts", ctypes.c_int32)]
+                ("locked", ctypes.c_int32), ("cholqr_shifts", ctypes.c_int32),
+                ("filter_col_steps_forced", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

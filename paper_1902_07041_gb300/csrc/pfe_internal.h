@@ -224,7 +224,7 @@ struct SolveState {
   double *dtheta = nullptr, *dpth = nullptr;
   int32_t q = 0, act = 0, nl = 0, it = 0, prev_count = -1, fp64_sweeps = 0;
   int32_t k64 = 0;  // mixed precision: the first k64 active columns use the FP64 filter
-  int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0;
+  int64_t ld = 0, matvecs = 0, f_launch = 0, f_cols64 = 0, f_cols32 = 0, f_cols_forced = 0;
   double t_start = 0, t_filter = 0, t_filter32 = 0, t_orth = 0, t_rr = 0, prev_worst = 1e300, window_est = -1.0;
   pfe_status result = PFE_E_NOCONV;
   double *X = nullptr, *Y = nullptr, *W = nullptr, *T0 = nullptr, *T1 = nullptr, *L = nullptr;

@@ -179,6 +179,7 @@ extern "C" pfe_status pfe_solve_sliced(pfe_ctx *ctx, int32_t nedges, const doubl
     sum.filter_launches += o.filter_launches;
     sum.filter_col_steps += o.filter_col_steps;
     sum.filter_col_steps_f32 += o.filter_col_steps_f32;
+    sum.filter_col_steps_forced += o.filter_col_steps_forced;
     sum.seconds_filter_f32 += o.seconds_filter_f32;
     sum.restarts += o.restarts;
     sum.cholqr_shifts += o.cholqr_shifts;

@@ -615,6 +615,7 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
   st.was64 = false;
   st.f_launch += m;
   st.f_cols32 += (int64_t)act * m;
+  st.f_cols_forced += (int64_t)act * (m - 1);
   st.matvecs += (int64_t)act * m;
   return check_launch(ctx, "defect-corrected filter");
 }
@@ -849,6 +850,7 @@ pfe_status solve_finish(pfe_ctx *ctx, int32_t *n_found) {
   o.filter_launches = st.f_launch;
   o.filter_col_steps = st.f_cols64;
   o.filter_col_steps_f32 = st.f_cols32;
+  o.filter_col_steps_forced = st.f_cols_forced;
   o.filter_shape_f64 = st.f_cols64 > 0 ? step_last_variant(0) : -1;
   o.filter_shape_f32 = st.f_cols32 > 0 ? step_last_variant(1) : -1;
   o.seconds_total = now_s() - st.t_start;
@@ -1792,24 +1794,58 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     // block Lanczos samples: every sample's solve on its own stream, the samples concurrently from
     // the host threads (their kernels overlap on the device); no shared graph
     std::vector<int32_t> nf(nsamples, 0);
-    // each sample's work buffers (several n x basis blocks) are released when its solve ends, so that
-    // only the solves in flight hold them; a sample that found no room beside the others runs again
-    // afterwards, one at a time
-    auto release_work = [](pfe_ctx *c) {
-      for (DBuf *b : {&c->w_X, &c->w_Y, &c->w_W, &c->w_T0, &c->w_T1, &c->w_T2, &c->w_small, &c->w_small2, &c->w_red,
-                      &c->w_cs_work, &c->w_ckpt, &c->w_rr, &c->w_gram, &c->w_bks[0], &c->w_bks[1], &c->w_bks[2],
-                      &c->w_bks[3], &c->w_bks[4]})
-        dbuf_free(*b);
+    // Work buffers (several n x basis blocks) pass from a finished sample to the next sample its host
+    // thread solves, so that only the solves in flight hold them and no device memory is freed while
+    // other samples run (cudaFree synchronises the device).  The samples go largest first, so a later
+    // sample rarely has to grow a buffer.  A sample that found no room beside the others runs again
+    // afterwards, one at a time.
+    auto work_bufs = [](pfe_ctx *c) {
+      return std::vector<DBuf *>{&c->w_X, &c->w_Y, &c->w_W, &c->w_T0, &c->w_T1, &c->w_T2, &c->w_small, &c->w_small2,
+                                 &c->w_red, &c->w_cs_work, &c->w_ckpt, &c->w_rr, &c->w_gram, &c->w_bks[0],
+                                 &c->w_bks[1], &c->w_bks[2], &c->w_bks[3], &c->w_bks[4]};
     };
-    for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) {
-      status[i] = bks_solve(ctxs[i], &nf[i]);
-      release_work(ctxs[i]);
-    });
+    std::vector<int32_t> order(nsamples);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return ctxs[x]->n > ctxs[y]->n; });
+    int32_t nt = nthreads;
+    if (nt <= 0) nt = (int32_t)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    nt = std::max(1, std::min(nt, nsamples));
+    std::atomic<int32_t> next{0};
+    auto worker = [&]() {
+      cudaSetDevice(c0->device);
+      std::vector<DBuf> carry;  // the buffers of this thread's previous sample
+      std::vector<DBuf> spare;  // smaller buffers the samples held before (freed when the thread ends)
+      for (int32_t t = next.fetch_add(1); t < nsamples; t = next.fetch_add(1)) {
+        const int32_t i = order[t];
+        auto bufs = work_bufs(ctxs[i]);
+        if (!carry.empty())
+          for (size_t b = 0; b < bufs.size(); ++b)
+            if (carry[b].bytes > bufs[b]->bytes) std::swap(*bufs[b], carry[b]);  // the sample takes the larger
+        for (DBuf &b : carry)
+          if (b.p) spare.push_back(b);
+        carry.clear();
+        status[i] = bks_solve(ctxs[i], &nf[i]);
+        cudaStreamSynchronize(ctxs[i]->stream);  // its kernels are done with the buffers
+        for (DBuf *b : bufs) {
+          carry.push_back(*b);
+          *b = DBuf{};
+        }
+      }
+      for (DBuf &b : carry) dbuf_free(b);
+      for (DBuf &b : spare) dbuf_free(b);
+    };
+    if (nt == 1) {
+      worker();
+    } else {
+      std::vector<std::thread> pool;
+      for (int32_t t = 0; t < nt; ++t) pool.emplace_back(worker);
+      for (auto &th : pool) th.join();
+    }
     for (int32_t i = 0; i < nsamples; ++i) {
       if (status[i] != PFE_E_NOMEM) continue;
       cudaGetLastError();  // the failed allocation's error state
       status[i] = bks_solve(ctxs[i], &nf[i]);
-      release_work(ctxs[i]);
+      for (DBuf *b : work_bufs(ctxs[i])) dbuf_free(*b);
     }
     pfe_status first = PFE_OK;
     for (int32_t i = 0; i < nsamples; ++i) {

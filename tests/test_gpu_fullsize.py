@@ -23,10 +23,18 @@ def _device():
     pfe.load()
 
 
-def test_bench_workload_full_size():
+@pytest.fixture(scope="module")
+def workload():
     g = glassgen.generate(100_000, 1)
-    rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
+    return g, pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat), oracle.csr_from_springs(g)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_bench_workload_full_size(workload, precision):
+    """precision 0: the FP64 form bench.py times; 2: the defect-corrected FP32 filter it reports beside."""
+    g, (rp, ci, vals), H = workload
     ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
+    pfe.pfe_set_param(ctx, pfe.PFE_P_PRECISION, precision)
     try:
         lmax, _ = pfe.pfe_estimate(ctx)
         a, b = 0.02 * lmax, 0.0214 * lmax
@@ -34,13 +42,13 @@ def test_bench_workload_full_size():
         nf, _ = pfe.pfe_solve(ctx)
         lam, V, res = pfe.pfe_get_eigenpairs(ctx, g.n, nf)
         st = pfe.pfe_get_stats(ctx)
-        H = oracle.csr_from_springs(g)
         assert nf > 500 and np.all((lam >= a) & (lam <= b)) and np.all(np.diff(lam) >= 0)
         # residuals, recomputed on the CPU
         r = oracle.residuals(H, lam, V)
         assert np.all(r <= 1e-8 * lmax)
         assert np.allclose(r, res, rtol=1e-3, atol=1e-14 * lmax)
-        assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-5
+        # orthonormality: every locked block is CholQR2-orthonormal and projected against the earlier ones
+        assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-9
         # the count against the stochastic estimate of Sec. 2.4 (M = 30 vectors: a few standard errors)
         assert abs(nf - st["count_estimate"]) <= 0.15 * nf
         # completeness: three applications of the solver's filter to a fresh random block, the found

@@ -415,12 +415,13 @@ def test_solve_batch_block_lanczos_members():
 
 
 def test_solve_batch_mixed_precision_members():
-    """A batch whose members use different filter precisions still matches the exact eigenpairs."""
-    gs = [glassgen.generate(n, 40 + i) for i, n in enumerate((200, 260))]
+    """A batch whose members use different filter precisions (FP64, the FP64 hand-over, the defect-
+    corrected FP32 filter) still matches the exact eigenpairs."""
+    gs = [glassgen.generate(n, 40 + i) for i, n in enumerate((200, 260, 230))]
     ctxs = []
     try:
         for i, g in enumerate(gs):
-            ctx, _ = make_ctx(g, PRECISION=i % 2)
+            ctx, _ = make_ctx(g, PRECISION=i % 3)
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, 0.05 * lmax, 0.12 * lmax)
             ctxs.append(ctx)
