@@ -314,7 +314,7 @@ bool aligned(const void *p, size_t a) { return p == nullptr || (reinterpret_cast
 // A forced shape (set_step_variant) wins; otherwise the autotuner's choice for (type, columns per
 // lane, column chunks, rank-1 form present) is used, and the default 0 before any tuning.
 namespace {
-constexpr int kVariants = 7, kR1Variants = 3;
+constexpr int kVariants = 7, kR1Variants = 4;
 int g_forced[2] = {-1, -1};  // [double, float]
 std::mutex g_tune_mu;
 std::mutex g_tune_run_mu;
@@ -329,6 +329,11 @@ int pick_variant(int is_float, int cpl, int32_t nchunk, bool r1) {
 }  // namespace
 
 void set_step_variant(int is_float, int variant) { g_forced[is_float ? 1 : 0] = variant; }
+
+bool step_prefers_tiled(int32_t k, int64_t ld) {
+  const int cpl = (k > 64 && ld % 4 == 0) ? 4 : ((k > 32 && ld % 2 == 0) ? 2 : 1);
+  return pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), true) == kVariants + 3;
+}
 int step_variant(int is_float) { return g_forced[is_float ? 1 : 0]; }
 
 namespace {

@@ -52,6 +52,13 @@ struct Bsr {
   const int32_t *ci1 = nullptr;
   const T *u = nullptr;
   const T *dg = nullptr;
+  // tiles of 32 atoms for the shared-memory staged FP32 step (r1_tiled.cu): the union of each tile's
+  // neighbourhoods, the slot of every off-diagonal block's column and of every atom in its tile
+  const int32_t *tile_ptr = nullptr;
+  const int32_t *tile_atoms = nullptr;
+  const uint16_t *slot1 = nullptr;
+  const uint16_t *self_slot = nullptr;
+  int32_t tile_umax = 0;
 };
 
 // Step modes of the fused BSR kernel (row-major n x k multivectors with row stride ld):
@@ -78,6 +85,17 @@ void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, c
 template <typename T>
 void dispatch_r1(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
                  T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s);
+// the FP32 step on the rank-1 form with each tile's neighbour rows staged in shared memory (shape 10);
+// F, fs non-null add the forcing term fs[c] F of the defect correction
+bool r1_tiled_usable(const Bsr<float> &A);
+void launch_r1_tiled(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W, float *Z,
+                     float *Y, const float *F, const float *fs, float alpha, float beta, float g0, float g1,
+                     cudaStream_t s);
+void build_r1_tiles(int32_t n_atoms, const std::vector<int32_t> &rp1, const std::vector<int32_t> &ci1,
+                    std::vector<int32_t> &tile_ptr, std::vector<int32_t> &tile_atoms, std::vector<uint16_t> &slot1,
+                    std::vector<uint16_t> &self_slot, int32_t *umax);
+// true when the autotuner chose the staged shape for FP32 steps on k columns
+bool step_prefers_tiled(int32_t k, int64_t ld);
 // rank-1 form of alpha (H - shift I); *bad (device) is set to 1 if an off-diagonal block is not -u u^T
 void launch_build_r1(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha, double shift,
                      int32_t *rp1, int32_t *ci1, double *u64, double *dg64, float *u32, float *dg32, int32_t *bad,
@@ -261,6 +279,8 @@ struct pfe_ctx {
   pfe::DBuf r1_rp, r1_ci, r1_u64, r1_dg64, r1_u32, r1_dg32, r1_flag;
   int r1_state = -1;
   bool r1_32 = false;
+  pfe::DBuf t_ptr, t_atoms, t_slot1, t_self;  // tiles of the staged FP32 step (built with the FP32 form)
+  int32_t t_umax = 0;
 
   // parameters
   int32_t p_degree = 0;

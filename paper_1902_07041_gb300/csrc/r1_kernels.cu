@@ -208,6 +208,12 @@ __global__ void k_build_r1(int32_t n_atoms, const int32_t *__restrict__ rp, cons
 template <typename T>
 void dispatch_r1(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
                  T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {  // shape 10: the neighbour rows of a tile staged in shared memory
+    if (variant == 3 && mode != MODE_ADJ && r1_tiled_usable(A)) {
+      launch_r1_tiled(A, mode, k, ld, X, W, Z, Y, nullptr, nullptr, alpha, beta, g0, g1, s);
+      return;
+    }
+  }
   if (cpl == 4)
     dispatch_r1_variant<T, (sizeof(T) == 4 ? 4 : 2)>(variant, A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s);
   else if (cpl == 2)

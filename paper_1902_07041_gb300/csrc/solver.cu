@@ -70,6 +70,13 @@ Bsr<float> bsr_Hs32(const pfe_ctx *ctx) {
     A.ci1 = ctx->r1_ci.as<int32_t>();
     A.u = ctx->r1_u32.as<float>();
     A.dg = ctx->r1_dg32.as<float>();
+    if (ctx->t_umax > 0) {
+      A.tile_ptr = ctx->t_ptr.as<int32_t>();
+      A.tile_atoms = ctx->t_atoms.as<int32_t>();
+      A.slot1 = ctx->t_slot1.as<uint16_t>();
+      A.self_slot = ctx->t_self.as<uint16_t>();
+      A.tile_umax = ctx->t_umax;
+    }
   }
   return A;
 }
@@ -197,6 +204,38 @@ pfe_status ensure_lmax(pfe_ctx *ctx) {
   return PFE_OK;
 }
 
+// Tiles of the shared-memory staged FP32 step (r1_tiled.cu), from the rank-1 pattern; once per context
+// (the pattern does not change with the transform).  Without tiles the staged shape is never used.
+pfe_status build_tiles(pfe_ctx *ctx) {
+  const int64_t noff = ctx->nnzb - ctx->N;
+  std::vector<int32_t> rp1((size_t)ctx->N + 1), ci1((size_t)noff);
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(rp1.data(), ctx->r1_rp.p, sizeof(int32_t) * rp1.size(), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(ci1.data(), ctx->r1_ci.p, sizeof(int32_t) * ci1.size(), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<int32_t> tptr, tatoms;
+  std::vector<uint16_t> slot1, self;
+  int32_t umax = 0;
+  build_r1_tiles(ctx->N, rp1, ci1, tptr, tatoms, slot1, self, &umax);
+  if (umax <= 0) return PFE_OK;
+  RESERVE(int32_t, dp, ctx->t_ptr, tptr.size());
+  RESERVE(int32_t, da, ctx->t_atoms, tatoms.size());
+  RESERVE(uint16_t, ds, ctx->t_slot1, std::max<size_t>(slot1.size(), 1));
+  RESERVE(uint16_t, dself, ctx->t_self, self.size());
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(dp, tptr.data(), sizeof(int32_t) * tptr.size(), cudaMemcpyHostToDevice, ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(da, tatoms.data(), sizeof(int32_t) * tatoms.size(), cudaMemcpyHostToDevice,
+                                    ctx->stream));
+  if (!slot1.empty())
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(ds, slot1.data(), sizeof(uint16_t) * slot1.size(), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaMemcpyAsync(dself, self.data(), sizeof(uint16_t) * self.size(), cudaMemcpyHostToDevice,
+                                    ctx->stream));
+  PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));  // the host vectors must outlive the copies
+  ctx->t_umax = umax;
+  return PFE_OK;
+}
+
 pfe_status ensure_hs(pfe_ctx *ctx, bool need32) {
   PFE_TRY(ensure_lmax(ctx));
   const bool same = ctx->hs_c == ctx->tc && ctx->hs_d == ctx->td;
@@ -234,6 +273,7 @@ pfe_status ensure_hs(pfe_ctx *ctx, bool need32) {
     PFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->r1_state = hbad ? 0 : 1;
     ctx->r1_32 = with32;
+    if (!hbad && with32 && ctx->t_umax == 0) PFE_TRY(build_tiles(ctx));
     if (hbad) {
       for (DBuf *b : {&ctx->r1_rp, &ctx->r1_ci, &ctx->r1_u64, &ctx->r1_dg64, &ctx->r1_u32, &ctx->r1_dg32})
         dbuf_free(*b);
@@ -596,6 +636,8 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
   cudaEventRecord(st.ev32[0], s);
   const Bsr<float> A = bsr_Hs32(ctx);
   launch_defect_prep(n, act, kd, st.X, st.W, ld, st.dtheta, 1.0 / ctx->td, g[1], st.X32, st.B32a, st.R32, st.Y32, s);
+  tune_step<float>(A, act, ld, st.X32, st.B32b, s);  // B32b is free until step 1
+  const bool tiled = step_prefers_tiled(act, ld) && r1_tiled_usable(A);
   if (kp > 0)  // t_1 = A t_0 / 2 and y = g0 t_0 + g1 t_1 for the plain columns
     launch_bsr_step<float>(A, MODE_FIRST, kp, ld, st.X32 + kd, nullptr, st.B32a + kd, st.Y32 + kd, 0.5f, 0.f,
                            (float)g[0], (float)g[1], s);
@@ -604,8 +646,13 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
   for (int32_t j = 1; j < m; ++j) {
     float *out = (tprev == st.X32) ? st.B32b : const_cast<float *>(tprev);
     const bool even = (j % 2) == 0, last = j == m - 1;
-    launch_defect_step(A, even ? MODE_STEP_ACC : MODE_STEP, act, ld, tcur, tprev, out, (even || last) ? st.Y32 : nullptr,
-                       st.R32, st.dfs + (size_t)j * ld, (float)g[j], (float)g[j + 1], s);
+    if (tiled)
+      launch_r1_tiled(A, even ? MODE_STEP_ACC : MODE_STEP, act, ld, tcur, tprev, out, (even || last) ? st.Y32 : nullptr,
+                      st.R32, st.dfs + (size_t)j * ld, 1.f, -1.f, (float)g[j], (float)g[j + 1], s);
+    else
+      launch_defect_step(A, even ? MODE_STEP_ACC : MODE_STEP, act, ld, tcur, tprev, out,
+                         (even || last) ? st.Y32 : nullptr, st.R32, st.dfs + (size_t)j * ld, (float)g[j], (float)g[j + 1],
+                         s);
     tprev = tcur;
     tcur = out;
   }
@@ -1281,7 +1328,8 @@ void pfe_destroy(pfe_ctx *ctx) {
                   &ctx->w_f32d, &ctx->w_ckpt, &ctx->w_rr, &ctx->w_gram,
                   &ctx->w_bks[0], &ctx->w_bks[1], &ctx->w_bks[2], &ctx->w_bks[3], &ctx->w_bks[4],
                   &ctx->r1_rp, &ctx->r1_ci, &ctx->r1_u64, &ctx->r1_dg64, &ctx->r1_u32, &ctx->r1_dg32,
-                  &ctx->r1_flag, &ctx->w_slice[0], &ctx->w_slice[1]};
+                  &ctx->r1_flag, &ctx->w_slice[0], &ctx->w_slice[1], &ctx->w_f32e, &ctx->w_defect, &ctx->w_tau,
+                  &ctx->t_ptr, &ctx->t_atoms, &ctx->t_slot1, &ctx->t_self};
   for (DBuf *b : bufs) dbuf_free(*b);
   for (int e = 0; e < 4; ++e)
     if (ctx->solve.ev[e]) cudaEventDestroy(ctx->solve.ev[e]);
@@ -1439,8 +1487,8 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       break;
     case PFE_P_STEP_SHAPE_F64:
     case PFE_P_STEP_SHAPE_F32:
-      if (!(v == -1 || (v >= 0 && v <= 9 && v == std::floor(v))))
-        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..9");
+      if (!(v == -1 || (v >= 0 && v <= 10 && v == std::floor(v))))
+        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..10");
       set_step_variant(key == PFE_P_STEP_SHAPE_F32, (int)v);
       break;
     default:

@@ -92,10 +92,11 @@ def test_filter_fp64_parity(N, seed, k, m):
         pfe.pfe_destroy(ctx)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_filter_every_kernel_shape(shape):
     """Each kernel shape of the fused step (forced instead of autotuned), FP64 and FP32, ragged k;
-    shapes 7-9 run on the rank-1 form of the spring network's operator."""
+    shapes 7-10 run on the rank-1 form of the spring network's operator, shape 10 (FP32) with each
+    tile's neighbour rows staged in shared memory (333 atoms: a ragged last tile of 13)."""
     g = glassgen.generate(333, 13)
     ctx, _ = make_ctx(g, LAMBDA_MAX=0.25)
     try:
@@ -328,14 +329,20 @@ def test_solve_mixed_precision_matches_fp64_accuracy(overlap):
     assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] > 0  # both precisions were used
 
 
-@pytest.mark.parametrize("N,seed,lo,hi", [(300, 5, 0.05, 0.12), (1000, 0, 0.02, 0.05)])
-def test_solve_defect_corrected_fp32_filter_reaches_fp64_accuracy(N, seed, lo, hi):
+@pytest.mark.parametrize("N,seed,lo,hi,shape", [(300, 5, 0.05, 0.12, -1), (1000, 0, 0.02, 0.05, -1),
+                                                (1000, 0, 0.02, 0.05, 10)])
+def test_solve_defect_corrected_fp32_filter_reaches_fp64_accuracy(N, seed, lo, hi, shape):
     """PRECISION 2: every filter application runs in FP32 (below the hand-over residual by defect
     correction: x p(theta) in FP64 plus the recurrence on the residual in FP32).  The plain FP32 filter
     alone stalls near its rounding level (~1e-4 of lambda_max); reaching the 1e-8 residuals, the exact
     count and the 1e-10 eigenvalues with no FP64 filter sweep shows the correction at work."""
-    st = _solve_and_check(glassgen.generate(N, seed), lo, hi, precision=2)
+    try:  # shape 10: the forced steps too run with the tile's neighbour rows in shared memory
+        st = _solve_and_check(glassgen.generate(N, seed), lo, hi, precision=2, STEP_SHAPE_F32=shape)
+    finally:
+        ctx, _ = make_ctx(glassgen.generate(20, 1), STEP_SHAPE_F32=-1)  # the shape is process-wide
+        pfe.pfe_destroy(ctx)
     assert st["filter_col_steps_f32"] > 0 and st["filter_col_steps"] == 0 and st["fp64_sweeps"] == 0
+    assert st["filter_col_steps_forced"] > 0
 
 
 @pytest.mark.parametrize("block", [16, 64])
