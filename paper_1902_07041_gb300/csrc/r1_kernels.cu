@@ -209,7 +209,8 @@ template <typename T>
 void dispatch_r1(int cpl, int variant, const Bsr<T> &A, int mode, int32_t k, int64_t ld, const T *X, const T *W, T *Z,
                  T *Y, T alpha, T beta, T g0, T g1, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {  // shape 10: the neighbour rows of a tile staged in shared memory
-    if (variant == 3 && mode != MODE_ADJ && r1_tiled_usable(A)) {
+    if (variant == 3 && mode != MODE_ADJ && r1_tiled_usable(A) && ld % 4 == 0 &&
+        (reinterpret_cast<uintptr_t>(X) & 15) == 0) {  // 16-byte cp.async pieces
       launch_r1_tiled(A, mode, k, ld, X, W, Z, Y, nullptr, nullptr, alpha, beta, g0, g1, s);
       return;
     }

@@ -637,7 +637,7 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
   const Bsr<float> A = bsr_Hs32(ctx);
   launch_defect_prep(n, act, kd, st.X, st.W, ld, st.dtheta, 1.0 / ctx->td, g[1], st.X32, st.B32a, st.R32, st.Y32, s);
   tune_step<float>(A, act, ld, st.X32, st.B32b, s);  // B32b is free until step 1
-  const bool tiled = step_prefers_tiled(act, ld) && r1_tiled_usable(A);
+  const bool tiled = step_prefers_tiled(act, ld) && r1_tiled_usable(A) && ld % 4 == 0;  // buffers 16-byte aligned
   if (kp > 0)  // t_1 = A t_0 / 2 and y = g0 t_0 + g1 t_1 for the plain columns
     launch_bsr_step<float>(A, MODE_FIRST, kp, ld, st.X32 + kd, nullptr, st.B32a + kd, st.Y32 + kd, 0.5f, 0.f,
                            (float)g[0], (float)g[1], s);
