@@ -451,9 +451,16 @@ pfe_status chol_factor(pfe_ctx *ctx, double *G, double *Rinv, int32_t k, bool *s
 // second buffer; *result points to whichever holds Q.  Pass 1: G = Y^T Y, Y R^{-1} -> tmp.
 // Pass 2 only if the Gram matrix of tmp deviates from I by more than 1e-13 (max entry), and
 // a third pass after a shifted factorisation.
-pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result, bool *shifted_out = nullptr) {
+// gram_out (optional): when the block after the first pass is already nearly orthonormal (its Gram
+// matrix G1 within 1e-3 of I, no shift), the second pass is left to the caller, which folds it into a
+// generalized Rayleigh-Ritz problem (X1^T H X1) c = theta G1 c: *gram_out then points to G1 (device,
+// k x k, valid until the next CholQR2) and *result to the once-orthonormalised block.  Otherwise
+// *gram_out is null and *result is orthonormal.
+pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, double **result, bool *shifted_out = nullptr,
+                   double **gram_out = nullptr) {
   *result = Y;
   if (shifted_out) *shifted_out = false;
+  if (gram_out) *gram_out = nullptr;
   if (k <= 0) return PFE_OK;
   cudaStream_t s = ctx->stream;
   RESERVE(double, G, ctx->w_small, (size_t)2 * k * k + 8);
@@ -469,6 +476,10 @@ pfe_status cholqr2(pfe_ctx *ctx, double *Y, double *tmp, int32_t k, int64_t ld, 
       PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&h, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
       PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
       if (h <= 1e-13 && !(any_shift && pass == 1)) break;
+      if (gram_out && pass == 1 && !any_shift && h <= 1e-3) {
+        *gram_out = G;
+        break;
+      }
     }
     bool shifted = false;
     PFE_TRY(chol_factor(ctx, G, Rinv, k, &shifted));
@@ -724,9 +735,10 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
   cudaEventRecord(st.ev[1], s);
   // ---- orthonormalise against the locked vectors and within the block
   PFE_TRY(project_out(ctx, st.L, st.nl, st.Y, act, ld));
+  double *G1 = nullptr;  // set: the block is once-orthonormalised, its Gram matrix G1 joins Rayleigh-Ritz
   {
     double *res = nullptr;
-    PFE_TRY(cholqr2(ctx, st.Y, st.T0, act, ld, &res));
+    PFE_TRY(cholqr2(ctx, st.Y, st.T0, act, ld, &res, nullptr, &G1));
     if (res != st.Y) std::swap(st.Y, st.T0);
   }
   std::swap(st.X, st.Y);
@@ -741,11 +753,20 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
     launch_gram(n, act, act, st.X, ld, st.W, ld, 1.0, 0.0, st.A, act, true, gw, s);
   }
   int lw = 0;
-  PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act,
-                                                  st.A, act, st.resid2, &lw));
-  RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
-  PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, st.A, act,
-                                       st.evals, work, lw, st.info));
+  if (G1) {
+    // the second CholQR2 pass folded in: A c = theta G1 c with c^T G1 c = 1, so X1 C is orthonormal
+    PFE_SOLVER_TRY(ctx, cusolverDnDsygvd_bufferSize(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                                    CUBLAS_FILL_MODE_UPPER, act, st.A, act, G1, act, st.resid2, &lw));
+    RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
+    PFE_SOLVER_TRY(ctx, cusolverDnDsygvd(ctx->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
+                                         CUBLAS_FILL_MODE_UPPER, act, st.A, act, G1, act, st.evals, work, lw, st.info));
+  } else {
+    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act,
+                                                    st.A, act, st.resid2, &lw));
+    RESERVE(double, work, ctx->w_cs_work, (size_t)std::max(lw, 1));
+    PFE_SOLVER_TRY(ctx, cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, act, st.A, act,
+                                         st.evals, work, lw, st.info));
+  }
   launch_update(n, act, act, st.X, ld, st.A, act, 1.0, 0.0, st.Y, ld, s);
   std::swap(st.X, st.Y);
   // W = H X again on the rotated block: one BSR product instead of the n x q x q update W <- W Q
@@ -759,7 +780,9 @@ pfe_status solve_after_filter(pfe_ctx *ctx) {
   PFE_CUDA_TRY(ctx, cudaMemcpyAsync(st.hr2.data(), st.resid2, sizeof(double) * act, cudaMemcpyDeviceToHost, s));
   PFE_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, st.info, sizeof(int), cudaMemcpyDeviceToHost, s));
   PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  if (hinfo != 0) return pfe_fail(ctx, PFE_E_CUDA, "cusolverDnDsyevd did not converge (info " + std::to_string(hinfo) + ")");
+  if (hinfo != 0)
+    return pfe_fail(ctx, PFE_E_CUDA, std::string(G1 ? "cusolverDnDsygvd" : "cusolverDnDsyevd") + " failed (info " +
+                                         std::to_string(hinfo) + ")");
   float ms = 0;
   if (st.timed_filter) {
     cudaEventElapsedTime(&ms, st.ev[0], st.ev[1]);
