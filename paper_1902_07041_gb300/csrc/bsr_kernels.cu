@@ -340,6 +340,7 @@ namespace {
 std::atomic<int> g_last_variant[2] = {{-1}, {-1}};
 }
 int step_last_variant(int is_float) { return g_last_variant[is_float ? 1 : 0].load(); }
+void note_step_variant(int is_float, int variant) { g_last_variant[is_float ? 1 : 0].store(variant); }
 void reset_step_last_variant() {
   g_last_variant[0].store(-1);
   g_last_variant[1].store(-1);

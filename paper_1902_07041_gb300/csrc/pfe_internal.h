@@ -78,6 +78,7 @@ void set_step_variant(int is_float, int variant);
 int step_variant(int is_float);
 // shape of the last filter-step launch (FIRST or STEP mode) of this type (process-wide; -1 before any), and a reset
 int step_last_variant(int is_float);
+void note_step_variant(int is_float, int variant);  // record the shape of a step launched outside launch_bsr_step
 void reset_step_last_variant();
 template <typename T>
 void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, cudaStream_t s);

@@ -668,6 +668,7 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
     tcur = out;
   }
   launch_defect_combine(n, act, st.X, ld, st.dpth, st.Y32, st.Y, s);
+  if (m > 1) note_step_variant(1, tiled ? 10 : 8);  // the forced steps: staged (10) or as shape 8
   cudaEventRecord(st.ev32[1], s);
   st.timed32 = true;
   st.was64 = false;

@@ -317,6 +317,21 @@ def test_solve_config_n1000_fp64():
     _solve_and_check(glassgen.generate(1000, 0), 0.02, 0.05)
 
 
+@pytest.mark.parametrize("rule", [0, 1])
+def test_degree_rule(rule):
+    """DEGREE_RULE 0 keeps the degree of eq. (thresh) (r = sqrt(0.1)), the library's own host design of
+    it; 1 may only raise it (the work model's candidates start there).  Both solve exactly."""
+    g = glassgen.generate(1000, 0)
+    st = _solve_and_check(g, 0.02, 0.05, DEGREE_RULE=rule)
+    lmax = st["lambda_max"]
+    xi, eta = (0.02 * lmax - lmax / 2) / (lmax / 2), (0.05 * lmax - lmax / 2) / (lmax / 2)
+    m0, _ = pfe.pfe_design_filter("pq", xi, eta, eps=0.25 * (eta - xi), r=0.1 ** 0.5)
+    if rule == 0:
+        assert st["degree"] == m0
+    else:
+        assert m0 <= st["degree"] <= 4 * m0
+
+
 def test_solve_config_n1000_degree40():
     """The same workload with the fixed degree 40 (a weak filter: more iterations)."""
     _solve_and_check(glassgen.generate(1000, 0), 0.02, 0.05, DEGREE=40, WIDTH=256, MAX_ITERS=200)
