@@ -61,8 +61,13 @@ SOLVE_WORK = {
 # DRAM traffic per launch of the dominant kernel, measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on one GB300 for the launch shape the solve runs, keyed by the kernel's
 # source file hash: a changed kernel invalidates the number.  (kernel, columns, FP bytes) -> bytes.
-TRAFFIC = {}
-R1_SHAPES = (7, 8, 9)  # kernel shapes of the fused step that run on the rank-1 form
+TRAFFIC = {
+    # N = 100,000, k = 994 (the width of the bench solve's first iterations), shape 9: the mean of a STEP
+    # launch (8.75 GB) and a STEP_ACC launch (13.51 GB); algorithmic bytes of that mean launch 10.09 GB
+    ("k_r1_step<double>", 8): {"file": "paper_1902_07041_gb300/csrc/r1_kernels.cu", "src": "16fe97d2aadb0977",
+                                "bytes": 11131068288, "alg_bytes": 10086400320},
+}
+R1_SHAPES = (7, 8, 9, 10)  # kernel shapes of the fused step that run on the rank-1 form
 
 
 def _src_hash(rel):

@@ -89,9 +89,10 @@ enum {
                                same with two 3x3 blocks in flight per iteration, 4: neighbour rows staged
                                in shared memory by cp.async four blocks ahead (16-byte lanes), 5 and 6:
                                0 and 1 compiled for five resident CTAs per SM; 7, 8, 9: the rank-1
-                               form (PFE_P_RANK1) as 0, 5 and 2 (shape 0 when there is none); 10: FP32 on
-                               the rank-1 form, a CTA per 32 atoms x 32 columns with the rows of the
-                               tile's neighbourhood staged in shared memory (as 7 in FP64) */
+                               form (PFE_P_RANK1) as 0, 5 and 2 (shape 0 when there is none); 10 (only when
+                               set, never autotuned): FP32 on the rank-1 form, a CTA per 32 atoms x 32
+                               columns with the rows of the tile's neighbourhood staged in shared memory
+                               (as 7 in FP64) */
   PFE_P_STEP_SHAPE_F32 = 20, /* PROCESS-WIDE: the same for the FP32 filter step */
   PFE_P_METHOD = 21,        /* 0: filtered subspace iteration (Alg. 4, default); 1: thick-restart block
                                Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),

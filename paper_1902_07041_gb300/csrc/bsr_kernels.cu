@@ -314,7 +314,10 @@ bool aligned(const void *p, size_t a) { return p == nullptr || (reinterpret_cast
 // A forced shape (set_step_variant) wins; otherwise the autotuner's choice for (type, columns per
 // lane, column chunks, rank-1 form present) is used, and the default 0 before any tuning.
 namespace {
-constexpr int kVariants = 7, kR1Variants = 4;
+// The tuner times the full-block shapes 0-6, or the rank-1 shapes 7-9 when the operator has that form.
+// Shape 10 (FP32, rows staged in shared memory) runs only when forced: it measured 3.6x slower than
+// shape 8 (its load phase leaves 24 warps per SM waiting, where the gathers of shape 8 overlap).
+constexpr int kVariants = 7, kR1Variants = 3, kStagedVariant = 10;
 int g_forced[2] = {-1, -1};  // [double, float]
 std::mutex g_tune_mu;
 std::mutex g_tune_run_mu;
@@ -330,10 +333,7 @@ int pick_variant(int is_float, int cpl, int32_t nchunk, bool r1) {
 
 void set_step_variant(int is_float, int variant) { g_forced[is_float ? 1 : 0] = variant; }
 
-bool step_prefers_tiled(int32_t k, int64_t ld) {
-  const int cpl = (k > 64 && ld % 4 == 0) ? 4 : ((k > 32 && ld % 2 == 0) ? 2 : 1);
-  return pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), true) == kVariants + 3;
-}
+bool step_prefers_tiled(int32_t, int64_t) { return g_forced[1] == kStagedVariant; }
 int step_variant(int is_float) { return g_forced[is_float ? 1 : 0]; }
 
 namespace {
