@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--hi", type=float, default=0.026)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--solo", action="store_true", help="also time the samples solved one by one")
+    ap.add_argument("--no-batch", action="store_true", help="with --solo: time only the one-by-one solves")
     ap.add_argument("--threads", type=int, default=0, help="host threads for the per-sample steps (0: automatic)")
     ap.add_argument("--method", type=int, default=0, help="0 subspace iteration (lockstep), 1 block Lanczos")
     a = ap.parse_args()
@@ -52,29 +53,31 @@ def main():
             ctxs.append(ctx)
         return ctxs
 
-    ctxs = make_all()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nfs, st = pfe.pfe_solve_batch(ctxs)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    stats = [pfe.pfe_get_stats(c) for c in ctxs]
-    for c in ctxs:
-        pfe.pfe_destroy(c)
-    out = {"samples": a.samples, "atoms_total": int(sum(sizes)), "precision": a.precision, "method": a.method,
-           "status": st,
-           "batch_s": t_batch, "batch_filter_s": stats[0]["seconds_filter"],
-           "replays": stats[0]["batch_replays"], "modes_total": int(sum(nfs)),
-           "iterations_max": max(s["iterations"] for s in stats), "matvecs_total": sum(s["matvecs"] for s in stats),
-           "widths": [s["width"] for s in stats], "n_found": nfs}
+    out = {"samples": a.samples, "atoms_total": int(sum(sizes)), "precision": a.precision, "method": a.method}
+    if not a.no_batch:
+        ctxs = make_all()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nfs, st = pfe.pfe_solve_batch(ctxs)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        stats = [pfe.pfe_get_stats(c) for c in ctxs]
+        for c in ctxs:
+            pfe.pfe_destroy(c)
+        out.update({"status": st, "batch_s": t_batch, "batch_filter_s": stats[0]["seconds_filter"],
+                    "replays": stats[0]["batch_replays"], "modes_total": int(sum(nfs)),
+                    "iterations_max": max(s["iterations"] for s in stats),
+                    "matvecs_total": sum(s["matvecs"] for s in stats), "widths": [s["width"] for s in stats],
+                    "n_found": nfs})
     if a.solo:
         ctxs = make_all()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for c in ctxs:
-            pfe.pfe_solve(c, raise_on_error=False)
+        solo = [pfe.pfe_solve(c, raise_on_error=False) for c in ctxs]
         torch.cuda.synchronize()
         out["solo_s"] = time.perf_counter() - t0
+        out["solo_status"] = max(s for _, s in solo)
+        out["solo_modes_total"] = int(sum(nf for nf, _ in solo))
         for c in ctxs:
             pfe.pfe_destroy(c)
     print(json.dumps(out), flush=True)
