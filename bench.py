@@ -67,7 +67,7 @@ TRAFFIC = {
     ("k_r1_step<double>", 8): {"file": "paper_1902_07041_gb300/csrc/r1_kernels.cu", "src": "16fe97d2aadb0977",
                                 "bytes": 11131068288, "alg_bytes": 10086400320},
 }
-R1_SHAPES = (7, 8, 9, 10)  # kernel shapes of the fused step that run on the rank-1 form
+R1_SHAPES = (7, 8, 9, 10, 11)  # kernel shapes of the fused step that run on the rank-1 form
 
 
 def _src_hash(rel):

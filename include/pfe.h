@@ -92,7 +92,8 @@ enum {
                                form (PFE_P_RANK1) as 0, 5 and 2 (shape 0 when there is none); 10 (only when
                                set, never autotuned): FP32 on the rank-1 form, a CTA per 32 atoms x 32
                                columns with the rows of the tile's neighbourhood staged in shared memory
-                               (as 7 in FP64) */
+                               (as 7 in FP64); 11: the rank-1 form as 8 compiled for six resident CTAs per
+                               SM */
   PFE_P_STEP_SHAPE_F32 = 20, /* PROCESS-WIDE: the same for the FP32 filter step */
   PFE_P_METHOD = 21,        /* 0: filtered subspace iteration (Alg. 4, default); 1: thick-restart block
                                Lanczos on the filter operator (Sec. 2.5, the paper's Krylov-Schur solver),

@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "pfe_internal.h"
 #include "vec_io.cuh"
@@ -317,7 +318,8 @@ namespace {
 // The tuner times the full-block shapes 0-6, or the rank-1 shapes 7-9 when the operator has that form.
 // Shape 10 (FP32, rows staged in shared memory) runs only when forced: it measured 3.6x slower than
 // shape 8 (its load phase leaves 24 warps per SM waiting, where the gathers of shape 8 overlap).
-constexpr int kVariants = 7, kR1Variants = 3, kStagedVariant = 10;
+constexpr int kVariants = 7, kStagedVariant = 10, kSixCtaVariant = 11;
+constexpr int kR1Candidates[] = {7, 8, 9, 11};  // rank-1 shapes the tuner times (11: as 8 at six CTAs per SM)
 int g_forced[2] = {-1, -1};  // [double, float]
 std::mutex g_tune_mu;
 std::mutex g_tune_run_mu;
@@ -334,6 +336,11 @@ int pick_variant(int is_float, int cpl, int32_t nchunk, bool r1) {
 void set_step_variant(int is_float, int variant) { g_forced[is_float ? 1 : 0] = variant; }
 
 bool step_prefers_tiled(int32_t, int64_t) { return g_forced[1] == kStagedVariant; }
+
+bool step_prefers_six_ctas(int32_t k, int64_t ld) {
+  const int cpl = (k > 64 && ld % 4 == 0) ? 4 : ((k > 32 && ld % 2 == 0) ? 2 : 1);
+  return pick_variant(1, cpl, (k + 32 * cpl - 1) / (32 * cpl), true) == kSixCtaVariant;
+}
 int step_variant(int is_float) { return g_forced[is_float ? 1 : 0]; }
 
 namespace {
@@ -404,9 +411,14 @@ void tune_step(const Bsr<T> &A, int32_t k, int64_t ld, const T *X, T *scratch, c
   }
   float best = 1e30f;
   int best_v = r1 ? kVariants : 0;
+  std::vector<int> cands;
+  if (r1)
+    cands.assign(std::begin(kR1Candidates), std::end(kR1Candidates));
+  else
+    for (int v = 0; v < kVariants; ++v) cands.push_back(v);
   // with the rank-1 form only its shapes compete: they do a third fewer FMAs and read a third of
   // the matrix bytes of the full-block shapes
-  for (int v = r1 ? kVariants : 0; v < (r1 ? kVariants + kR1Variants : kVariants); ++v) {
+  for (int v : cands) {
     float t = 1e30f;
     for (int trial = 0; trial < 2; ++trial) {
       cudaEventRecord(e0, s);

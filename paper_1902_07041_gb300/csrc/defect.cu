@@ -21,13 +21,13 @@ namespace pfe {
 namespace {
 
 // One step of the recurrence with forcing, FP32, warp per (atom, column chunk) as the rank-1 step
-// kernel (five resident CTAs per SM):
+// kernel (MINB resident CTAs per SM: 5, or 6 when the tuner chose shape 11 for the plain step):
 //   Z = A X - W + fs[c] F                       (X = D_j, W = D_{j-1}, may alias Z; F = Rt)
 //   MODE_STEP:     Y += g1 Z  when Y is given   (odd steps: only the last one)
 //   MODE_STEP_ACC: Y += g0 X + g1 Z             (even steps: the input's term one step late)
 // R1: the operator's rank-1 form (u, dg); otherwise its full 3x3 blocks (vals).
-template <int CPL, int MODE, bool R1>
-__global__ void __launch_bounds__(256, 5) k_defect_step(int32_t n_atoms, const int32_t *__restrict__ rp,
+template <int CPL, int MODE, bool R1, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_defect_step(int32_t n_atoms, const int32_t *__restrict__ rp,
                                                         const int32_t *__restrict__ ci, const float *__restrict__ vals,
                                                         const float *__restrict__ u, const float *__restrict__ dg,
                                                         int32_t k, int64_t ld, int32_t nchunk,
@@ -168,7 +168,7 @@ __global__ void k_defect_combine(int64_t n, int32_t act, const double *__restric
   Y[off] = fma(pth[c], X[off], (double)Y32[off]);
 }
 
-template <int CPL>
+template <int CPL, int MINB>
 void dispatch_defect_cpl(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W, float *Z,
                          float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s) {
   const int32_t nchunk = (k + 32 * CPL - 1) / (32 * CPL);
@@ -177,7 +177,7 @@ void dispatch_defect_cpl(const Bsr<float> &A, int mode, int32_t k, int64_t ld, c
   const int32_t *rp = r1 ? A.rp1 : A.rp;
   const int32_t *ci = r1 ? A.ci1 : A.ci;
 #define PFE_DEFECT_LAUNCH(M, R)                                                                           \
-  PFE_LAUNCH k_defect_step<CPL, M, R><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, rp, ci, A.vals, A.u, A.dg, k, ld, \
+  PFE_LAUNCH k_defect_step<CPL, M, R, MINB><<<(unsigned)blocks, 256, 0, s>>>(A.n_atoms, rp, ci, A.vals, A.u, A.dg, k, ld, \
                                                                        nchunk, X, W, Z, Y, F, fs, g0, g1)
   if (mode == MODE_STEP_ACC) {
     if (r1) PFE_DEFECT_LAUNCH(MODE_STEP_ACC, true);
@@ -194,13 +194,15 @@ bool al16(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p
 }  // namespace
 
 void launch_defect_step(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W, float *Z,
-                        float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s) {
+                        float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s, bool six_ctas) {
   if (k <= 0 || A.n_atoms <= 0) return;
   const bool v4 = ld % 4 == 0 && al16(X) && al16(W) && al16(Z) && al16(Y) && al16(F) && al16(fs) && k > 64;
-  if (v4)
-    dispatch_defect_cpl<4>(A, mode, k, ld, X, W, Z, Y, F, fs, g0, g1, s);
+  if (v4 && six_ctas)
+    dispatch_defect_cpl<4, 6>(A, mode, k, ld, X, W, Z, Y, F, fs, g0, g1, s);
+  else if (v4)
+    dispatch_defect_cpl<4, 5>(A, mode, k, ld, X, W, Z, Y, F, fs, g0, g1, s);
   else
-    dispatch_defect_cpl<1>(A, mode, k, ld, X, W, Z, Y, F, fs, g0, g1, s);
+    dispatch_defect_cpl<1, 5>(A, mode, k, ld, X, W, Z, Y, F, fs, g0, g1, s);
 }
 
 void launch_defect_prep(int64_t n, int32_t act, int32_t kd, const double *X, const double *W, int64_t ld,

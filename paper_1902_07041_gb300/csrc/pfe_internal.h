@@ -97,6 +97,8 @@ void build_r1_tiles(int32_t n_atoms, const std::vector<int32_t> &rp1, const std:
                     std::vector<uint16_t> &self_slot, int32_t *umax);
 // true when the autotuner chose the staged shape for FP32 steps on k columns
 bool step_prefers_tiled(int32_t k, int64_t ld);
+// true when the autotuner chose the rank-1 FP32 step at six resident CTAs per SM (shape 11) for k columns
+bool step_prefers_six_ctas(int32_t k, int64_t ld);
 // rank-1 form of alpha (H - shift I); *bad (device) is set to 1 if an off-diagonal block is not -u u^T
 void launch_build_r1(int32_t n_atoms, const int32_t *rp, const int32_t *ci, const double *H, double alpha, double shift,
                      int32_t *rp1, int32_t *ci1, double *u64, double *dg64, float *u32, float *dg32, int32_t *bad,
@@ -175,7 +177,8 @@ void launch_batch_step(int cpl, int blocks, const BatchDesc *desc, int32_t nsamp
 // Mixed-precision filter by defect correction (defect.cu).  Step with forcing, FP32:
 //   Z = A X - W + fs[c] F;  MODE_STEP: Y += g1 Z (Y may be null);  MODE_STEP_ACC: Y += g0 X + g1 Z
 void launch_defect_step(const Bsr<float> &A, int mode, int32_t k, int64_t ld, const float *X, const float *W, float *Z,
-                        float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s);
+                        float *Y, const float *F, const float *fs, float g0, float g1, cudaStream_t s,
+                        bool six_ctas = false);
 // start of a block whose first kd of act columns are defect columns (Rt = (W - theta X) inv_d):
 //   defect: X32 = 0, B = Rt, F = Rt, Y32 = g1 Rt;  plain: X32 = X, F = 0
 void launch_defect_prep(int64_t n, int32_t act, int32_t kd, const double *X, const double *W, int64_t ld,

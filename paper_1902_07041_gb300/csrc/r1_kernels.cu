@@ -153,6 +153,7 @@ void dispatch_r1_variant(int variant, const Bsr<T> &A, int mode, int32_t k, int6
   switch (variant) {
     case 1: dispatch_r1_mode<T, CPL, 1, 5>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
     case 2: dispatch_r1_mode<T, CPL, 2, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
+    case 4: dispatch_r1_mode<T, CPL, 1, 6>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
     default: dispatch_r1_mode<T, CPL, 1, 1>(A, mode, k, ld, X, W, Z, Y, alpha, beta, g0, g1, s); break;
   }
 }

@@ -649,6 +649,7 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
   launch_defect_prep(n, act, kd, st.X, st.W, ld, st.dtheta, 1.0 / ctx->td, g[1], st.X32, st.B32a, st.R32, st.Y32, s);
   tune_step<float>(A, act, ld, st.X32, st.B32b, s);  // B32b is free until step 1
   const bool tiled = step_prefers_tiled(act, ld) && r1_tiled_usable(A) && ld % 4 == 0;  // buffers 16-byte aligned
+  const bool six = step_prefers_six_ctas(act, ld);
   if (kp > 0)  // t_1 = A t_0 / 2 and y = g0 t_0 + g1 t_1 for the plain columns
     launch_bsr_step<float>(A, MODE_FIRST, kp, ld, st.X32 + kd, nullptr, st.B32a + kd, st.Y32 + kd, 0.5f, 0.f,
                            (float)g[0], (float)g[1], s);
@@ -663,12 +664,12 @@ pfe_status solve_filter_defect(pfe_ctx *ctx, int32_t kd) {
     else
       launch_defect_step(A, even ? MODE_STEP_ACC : MODE_STEP, act, ld, tcur, tprev, out,
                          (even || last) ? st.Y32 : nullptr, st.R32, st.dfs + (size_t)j * ld, (float)g[j], (float)g[j + 1],
-                         s);
+                         s, six);
     tprev = tcur;
     tcur = out;
   }
   launch_defect_combine(n, act, st.X, ld, st.dpth, st.Y32, st.Y, s);
-  if (m > 1) note_step_variant(1, tiled ? 10 : 8);  // the forced steps: staged (10) or as shape 8
+  if (m > 1) note_step_variant(1, tiled ? 10 : (six ? 11 : 8));  // the forced steps: as shape 10, 11 or 8
   cudaEventRecord(st.ev32[1], s);
   st.timed32 = true;
   st.was64 = false;
@@ -1511,8 +1512,8 @@ pfe_status pfe_set_param(pfe_ctx *ctx, int key, double v) {
       break;
     case PFE_P_STEP_SHAPE_F64:
     case PFE_P_STEP_SHAPE_F32:
-      if (!(v == -1 || (v >= 0 && v <= 10 && v == std::floor(v))))
-        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..10");
+      if (!(v == -1 || (v >= 0 && v <= 11 && v == std::floor(v))))
+        return pfe_fail(ctx, PFE_E_ARG, "STEP_SHAPE must be -1 (autotuned) or 0..11");
       set_step_variant(key == PFE_P_STEP_SHAPE_F32, (int)v);
       break;
     default:

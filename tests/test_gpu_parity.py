@@ -92,11 +92,12 @@ def test_filter_fp64_parity(N, seed, k, m):
         pfe.pfe_destroy(ctx)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 def test_filter_every_kernel_shape(shape):
     """Each kernel shape of the fused step (forced instead of autotuned), FP64 and FP32, ragged k;
-    shapes 7-10 run on the rank-1 form of the spring network's operator, shape 10 (FP32) with each
-    tile's neighbour rows staged in shared memory (333 atoms: a ragged last tile of 13)."""
+    shapes 7-11 run on the rank-1 form of the spring network's operator, shape 10 (FP32) with each
+    tile's neighbour rows staged in shared memory (333 atoms: a ragged last tile of 13), shape 11 at six
+    resident CTAs per SM."""
     g = glassgen.generate(333, 13)
     ctx, _ = make_ctx(g, LAMBDA_MAX=0.25)
     try:
