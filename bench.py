@@ -59,20 +59,28 @@ SOLVE_WORK = {
 }
 
 # DRAM traffic per launch of the dominant kernel, measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on one GB300 for the launch shape the solve runs, keyed by the kernel's
-# source file hash: a changed kernel invalidates the number.  (kernel, columns, FP bytes) -> bytes.
+# dram__bytes_write.sum) on one GB300 for the launch shape the solve runs, keyed by a hash of the
+# kernel's source text: a changed kernel invalidates the number.  (kernel, FP bytes) -> bytes.
 TRAFFIC = {
     # N = 100,000, k = 994 (the width of the bench solve's first iterations), shape 9: the mean of a STEP
     # launch (8.75 GB) and a STEP_ACC launch (13.51 GB); algorithmic bytes of that mean launch 10.09 GB
-    ("k_r1_step<double>", 8): {"file": "paper_1902_07041_gb300/csrc/r1_kernels.cu", "src": "16fe97d2aadb0977",
+    ("k_r1_step<double>", 8): {"file": "paper_1902_07041_gb300/csrc/r1_kernels.cu",
+                                "begin": "template <typename T, int CPL, int MODE, int UNROLL, int MINB>",
+                                "end": "template <typename T, int CPL, int UNROLL, int MINB>\nvoid dispatch_r1_mode",
+                                "src": "2288ce777daee821",
                                 "bytes": 11131068288, "alg_bytes": 10086400320},
 }
 R1_SHAPES = (7, 8, 9, 10, 11)  # kernel shapes of the fused step that run on the rank-1 form
 
 
-def _src_hash(rel):
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _src_hash(rel, begin, end):
+    """Hash of the source text of one kernel: from the line that starts with `begin` to the one that
+    starts with `end` (the code that follows it)."""
+    with open(os.path.join(ROOT, rel)) as f:
+        s = f.read()
+    i = s.find(begin)
+    j = s.find(end, i + 1) if i >= 0 else -1
+    return hashlib.sha256(s[i:j].encode()).hexdigest()[:16] if i >= 0 and j > i else None
 
 
 def peaks():
@@ -565,7 +573,7 @@ def run_native(args, wl):
     kname = "k_r1_step<double>" if r1 else "k_bsr_step<double>"
     tr = TRAFFIC.get((kname, 8))
     traffic = None
-    if tr and tr["src"] == _src_hash(tr["file"]):
+    if tr and tr["src"] == _src_hash(tr["file"], tr["begin"], tr["end"]):
         traffic = tr["bytes"] * b_avg / tr["alg_bytes"]  # scaled from the captured launch to the average one
     roof = {"bound": "alu", "kernel": kname + " (fused Chebyshev step, shape %d)" % st["filter_shape_f64"],
             "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
