@@ -49,8 +49,11 @@ def test_bench_workload_full_size(workload, precision):
         assert np.allclose(r, res, rtol=1e-3, atol=1e-14 * lmax)
         # orthonormality: every locked block is CholQR2-orthonormal and projected against the earlier ones
         assert np.max(np.abs(V.T @ V - np.eye(nf))) <= 1e-9
-        # the count against the stochastic estimate of Sec. 2.4 (M = 30 vectors: a few standard errors)
-        assert abs(nf - st["count_estimate"]) <= 0.15 * nf
+        # the count against the stochastic estimate of Sec. 2.4: for normalised Gaussian vectors one
+        # sample of n v^T psi v has variance about 2 sum psi_i^2 <= 2 x (count + window), so M = 30
+        # vectors give a standard error near sqrt(2 x 1,500 / 30) = 10 here; 6 % of the count is three
+        # standard errors plus the smoothing of the degree-100 series
+        assert abs(nf - st["count_estimate"]) <= 0.06 * nf
         # completeness: three applications of the solver's filter to a fresh random block, the found
         # space projected out before and after each; then Rayleigh-Ritz with H.  A missed eigenpair
         # would give a Ritz pair whose residual interval [theta - r, theta + r] lies inside [a, b]
