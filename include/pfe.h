@@ -350,7 +350,10 @@ pfe_status pfe_probe_fp64_fma(int32_t iters, int32_t reps, void *stream, double 
  * the next sample its thread solves (its eigenvectors stay), so only the solves in flight hold them
  * and none is freed while others run, and a sample that ran out of device memory beside the others
  * is solved again afterwards, alone.  All contexts of a batch select the same method (PFE_E_ARG otherwise).
- * In the stats of every sample seconds_filter is the batch's shared filter time.
+ * In the stats of every sample seconds_filter is the batch's shared filter time.  In the lockstep
+ * subspace iteration too, a sample that ran out of device memory beside the others is solved again
+ * after the batch, alone (its stats are then its own solve's), and every sample releases its work
+ * buffers when the batch ends (its eigenvectors stay).
  * Returns the first failing status (the other samples still run). */
 pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found);
 

@@ -1927,8 +1927,23 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     }
     return first;
   }
-  // set-up of every sample (filter design, width, buffers, start block)
+  // the work buffers of a subspace-iteration solve (the locked vectors L hold the results and stay)
+  auto release_si_work = [](pfe_ctx *c) {
+    cudaStreamSynchronize(c->stream);
+    for (DBuf *b : {&c->w_X, &c->w_Y, &c->w_W, &c->w_T0, &c->w_T1, &c->w_rr, &c->w_red, &c->w_gram, &c->w_small,
+                    &c->w_small2, &c->w_cs_work, &c->w_f32a, &c->w_f32b, &c->w_f32c, &c->w_f32d, &c->w_f32e,
+                    &c->w_defect, &c->w_tau})
+      dbuf_free(*b);
+  };
+  // set-up of every sample (filter design, width, buffers, start block); a sample that failed gives
+  // back what it had reserved
   for_each_sample(c0->device, nsamples, nthreads, [&](int32_t i) { status[i] = solve_setup(ctxs[i]); });
+  for (int32_t i = 0; i < nsamples; ++i)
+    if (status[i] != PFE_OK) {
+      release_si_work(ctxs[i]);
+      dbuf_free(ctxs[i]->L);  // no results yet
+    }
+  cudaGetLastError();  // a failed allocation's error state
   BatchPlan plan;
   pfe_status bst = batch_plan_init(c0, ctxs, nsamples, status, &plan);
   if (bst != PFE_OK) {
@@ -1973,8 +1988,21 @@ pfe_status pfe_solve_batch(pfe_ctx **ctxs, int32_t nsamples, int32_t *n_found) {
     ctxs[i]->stats.seconds_filter = t_batch_filter;  // shared by the whole batch
     ctxs[i]->stats.batch_replays = batch_replays;
     if (n_found) n_found[i] = (status[i] == PFE_OK) ? nf : 0;
-    if (fs != PFE_OK && first == PFE_OK) first = fs;
+    status[i] = fs;
   }
+  // the batch is over: every sample gives back its work buffers; the samples that found no room
+  // beside the others are solved again, one at a time (pfe_solve), each releasing its buffers after
+  for (int32_t i = 0; i < nsamples; ++i) release_si_work(ctxs[i]);
+  for (int32_t i = 0; i < nsamples; ++i) {
+    if (status[i] != PFE_E_NOMEM) continue;
+    cudaGetLastError();
+    int32_t nf = 0;
+    status[i] = pfe_solve(ctxs[i], &nf);
+    if (n_found) n_found[i] = (status[i] == PFE_OK || status[i] == PFE_E_CAPACITY) ? nf : 0;
+    release_si_work(ctxs[i]);
+  }
+  for (int32_t i = 0; i < nsamples; ++i)
+    if (status[i] != PFE_OK && first == PFE_OK) first = status[i];
   return first;
 }
 
