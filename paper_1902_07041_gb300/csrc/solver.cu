@@ -594,13 +594,22 @@ pfe_status solve_setup(pfe_ctx *ctx) {
     if (!st.ev[e]) PFE_CUDA_TRY(ctx, cudaEventCreate(&st.ev[e]));
   for (int e = 0; e < 2; ++e)
     if (!st.ev32[e]) PFE_CUDA_TRY(ctx, cudaEventCreate(&st.ev32[e]));
-  // start block (stream 0 of the seeded Philox normals) and its orthonormalisation
+  // start block: stream 0 of the seeded Philox normals, columns scaled to unit norm.  It is not
+  // orthonormalised: the first filter application maps it to p(Ht) X0, whose span is that of
+  // p(Ht) X0 R^-1 for any invertible R, and the filtered block is orthonormalised (CholQR2) anyway.
   launch_fill_normal<double>(ctx->p_seed, 0u, n, q, 0, st.X, ld, s);
   PFE_TRY(check_launch(ctx, "start block"));
   {
-    double *res = nullptr;
-    PFE_TRY(cholqr2(ctx, st.X, st.T0, q, ld, &res));
-    if (res != st.X) std::swap(st.X, st.T0);
+    RESERVE(double, dots, ctx->w_small, 2 * (size_t)q + 8);
+    launch_col_dots<double>(n, q, st.X, ld, st.X, ld, dots, st.red, s);
+    std::vector<double> nrm((size_t)q);
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(nrm.data(), dots, sizeof(double) * q, cudaMemcpyDeviceToHost, s));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (double &v : nrm) v = v > 0.0 ? 1.0 / std::sqrt(v) : 1.0;
+    PFE_CUDA_TRY(ctx, cudaMemcpyAsync(dots + q, nrm.data(), sizeof(double) * q, cudaMemcpyHostToDevice, s));
+    launch_scale_cols<double>(n, q, st.X, ld, dots + q, s);
+    PFE_TRY(check_launch(ctx, "start block scaling"));
+    PFE_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // nrm must outlive its copy
   }
   st.act = q;
   st.use64 = !st.fp32;
