@@ -2,7 +2,7 @@
 forms, block Lanczos) and compare each form's eigenpairs with the first form's, pair by pair.
 
     python -m paper_1902_07041_gb300.comparebench --n-atoms 500000 --seed 2 --lo 0.02 --hi 0.02047 \
-        --forms p2,p0 [--out per_pair.csv]
+        --forms p2,p0 [--out per_pair.csv] [--sliced 700]
 
 Forms: p0 = FP64 subspace iteration, p1 = mixed with the FP64 hand-over, p2 = mixed by defect
 correction, bks = block Lanczos (FP64).  Prints one JSON line per form (time to all eigenpairs by
@@ -30,12 +30,15 @@ def main():
     ap.add_argument("--hi", type=float, default=0.02047)
     ap.add_argument("--forms", default="p2,p0")
     ap.add_argument("--out", default="")
+    ap.add_argument("--sliced", type=int, default=0,
+                    help="spectrum slicing (pfe_solve_sliced) with about this many eigenvalues a slice")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     g = glassgen.generate(a.n_atoms, a.seed)
     rp, ci, vals = pfe.pfe_springs_to_bsr(g.n_atoms, g.bi, g.bj, g.k, g.rhat)
     n = g.n
-    results = {}
+    ref = None  # the first form: (name, eigenvalues, residuals, eigenvectors, lambda_max)
+    rows, hdr = [], []
     for form in a.forms.split(","):
         ctx = pfe.pfe_create(g.n_atoms, rp, ci, vals, g.mass)
         try:
@@ -48,7 +51,11 @@ def main():
             e0.record()
             lmax, _ = pfe.pfe_estimate(ctx)
             pfe.pfe_set_interval(ctx, a.lo * lmax, a.hi * lmax)
-            nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
+            if a.sliced > 0:
+                pfe.pfe_set_param(ctx, pfe.PFE_P_SLICE_TARGET, a.sliced)
+                nf, st = pfe.pfe_solve_sliced(ctx, raise_on_error=False)
+            else:
+                nf, st = pfe.pfe_solve(ctx, raise_on_error=False)
             e1.record()
             torch.cuda.synchronize()
             stats = pfe.pfe_get_stats(ctx)
@@ -57,17 +64,17 @@ def main():
         finally:
             pfe.pfe_destroy(ctx)
         torch.cuda.synchronize()
-        results[form] = (lam, res, V[:nf], lmax)
-        print(json.dumps({"form": form, "n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi,
+        V = V[:nf]
+        print(json.dumps({"form": form, "n_atoms": a.n_atoms, "seed": a.seed, "lo": a.lo, "hi": a.hi, "sliced": a.sliced,
                           "seconds": e0.elapsed_time(e1) / 1e3, "status": st, "n_found": nf,
                           "max_rel_residual": float(res.max() / lmax) if nf else 0.0, **stats}), flush=True)
-    forms = list(results)
-    ref = forms[0]
-    lam0, res0, V0, lmax0 = results[ref]
-    rows = [lam0, res0 / lmax0]
-    for form in forms[1:]:
-        lam, res, V, lmax = results[form]
-        out = {"compare": form, "with": ref, "n_found": [int(lam0.size), int(lam.size)]}
+        if ref is None:  # every later form is compared with this one as soon as it has finished
+            ref = (form, lam, res, V, lmax)
+            rows += [lam, res / lmax]
+            hdr += ["lambda_" + form, "rel_residual_" + form]
+            continue
+        name0, lam0, _, V0, _ = ref
+        out = {"compare": form, "with": name0, "n_found": [int(lam0.size), int(lam.size)]}
         if lam.size == lam0.size and lam.size > 0:
             rel = np.abs(lam - lam0) / np.abs(lam0)
             # sine of the largest principal angle between the two spaces: ||V - V0 (V0^T V)||_2
@@ -77,12 +84,12 @@ def main():
             out.update({"max_eig_rel_diff": float(rel.max()), "median_eig_rel_diff": float(np.median(rel)),
                         "subspace_sin_max": sin_max})
             rows += [lam, res / lmax, rel]
+            hdr += ["lambda_" + form, "rel_residual_" + form, "eig_rel_diff_" + form]
             del P, D
         print(json.dumps(out), flush=True)
-    if a.out and all(r.size == lam0.size for r in rows):
-        hdr = ["lambda_" + ref, "rel_residual_" + ref]
-        for form in forms[1:]:
-            hdr += ["lambda_" + form, "rel_residual_" + form, "eig_rel_diff_" + form]
+        del V
+        torch.cuda.empty_cache()
+    if a.out and rows and all(r.size == rows[0].size for r in rows):
         np.savetxt(a.out, np.column_stack(rows), delimiter=",", header=",".join(hdr), comments="", fmt="%.17g")
 
 
