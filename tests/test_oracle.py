@@ -370,6 +370,32 @@ def test_adjoint_symmetry_and_fd(small_glass):
         assert fd == pytest.approx(vb[p], rel=1e-5, abs=1e-7 * np.abs(vb).max())
 
 
+def test_adjoint_daleckii_krein(small_glass):
+    """The reverse sweep against the Daleckii-Krein formula for the derivative of a matrix function:
+    with Ht = Q diag(l) Q^T, d p(Ht)[E] = Q (F o (Q^T E Q)) Q^T, F_ij the divided difference of p at
+    l_i, l_j (p'(l_i) on coinciding values), so dL/dHt for L = <Ybar, p(Ht) X> is
+    Q (F o (Q^T Ybar X^T Q)) Q^T, and dL/dH = that / d.  Every stored entry is compared."""
+    g, H, A = small_glass
+    lmax = 1.01 * np.linalg.eigvalsh(A)[-1]
+    c = d = lmax / 2
+    coef = oracle.filter_coeffs(-0.9, -0.8, 0.03, 30, "jackson")
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((H.n, 3))
+    Yb = rng.standard_normal((H.n, 3))
+    _, vb = oracle.filter_adjoint(H, c, d, coef, X, Yb)
+    lam, Q = np.linalg.eigh((A - c * np.eye(H.n)) / d)
+    p = np.polynomial.chebyshev.chebval(lam, coef)
+    dp = np.polynomial.chebyshev.chebval(lam, np.polynomial.chebyshev.chebder(coef))
+    gap = lam[:, None] - lam[None, :]
+    close = np.abs(gap) < 1e-7
+    F = np.where(close, 0.5 * (dp[:, None] + dp[None, :]), (p[:, None] - p[None, :]) / np.where(close, 1.0, gap))
+    G = Q @ (F * (Q.T @ Yb @ X.T @ Q)) @ Q.T / d
+    rp, ci, _ = H.arrays()
+    rows = np.repeat(np.arange(H.n), np.diff(rp))
+    want = G[rows, ci]
+    assert np.abs(vb - want).max() <= 1e-9 * np.abs(want).max()
+
+
 def test_chain_springs_fd(small_glass):
     g, H, A = small_glass
     lmax = 1.01 * np.linalg.eigvalsh(A)[-1]
