@@ -681,7 +681,7 @@ double or_count_estimate(const or_csr *H, double c, double d, double xi, double 
 }
 
 /* ======================================================================================
- * Filtered subspace iteration with Rayleigh-Ritz on H and locking (Sec. 2.6, Alg. 1 step 2,
+ * Filtered subspace iteration with Rayleigh-Ritz on H and locking (Sec. 2.6, the Rayleigh-Ritz step of Alg. 1,
  * Alg. 4 with n_RR = 1, and the locking paragraph after Alg. 4).
  *
  * Per iteration, on the active (unlocked) columns:
