@@ -79,3 +79,17 @@ def test_reference_arm_runs_the_oracle_only():
     assert rec["ms_per_step"] * rec["steps"] <= 1e3 * rec["timed_wall_s"] * 1.001 + 1.0
     full = rec["cpu_baseline"]["oracle_full_solve_n1000"]
     assert full["status"] == 0 and full["n_found"] == 144  # the exact count of [0.02, 0.05] lambda_max
+
+
+def test_recorded_traffic_matches_the_current_kernel_source():
+    """roofline.traffic is only reported while the captured kernel's source text is unchanged: every
+    recorded DRAM capture must still hash to the kernel in the tree, and its algorithmic bytes must
+    be those of the launch model for the captured shape (N = 100,000, nnzb 1,128,572, k = 994)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for (kernel, fp_bytes), tr in bench.TRAFFIC.items():
+        assert bench._src_hash(tr["file"], tr["begin"], tr["end"]) == tr["src"], kernel
+        assert tr["bytes"] >= tr["alg_bytes"] > 0
+    tr = bench.TRAFFIC[("k_r1_step<double>", 8)]
+    assert bench.filter_work(100_000, 1_128_572, 994, 8, 8, rank1=True)[0] == tr["alg_bytes"]
