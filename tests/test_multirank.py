@@ -93,3 +93,34 @@ def test_recorded_traffic_matches_the_current_kernel_source():
         assert tr["bytes"] >= tr["alg_bytes"] > 0
     tr = bench.TRAFFIC[("k_r1_step<double>", 8)]
     assert bench.filter_work(100_000, 1_128_572, 994, 8, 8, rank1=True)[0] == tr["alg_bytes"]
+
+
+def test_clock_sampler_reads_median_under_load_and_throttle_reasons(tmp_path):
+    """The clocks field of the bench line from nvidia-smi's CSV (no GPU: the sampler's output file is
+    written here and its process is a stand-in)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 120, 2070, 90.1, 0x0, Not Active, Not Active, Not Active, Not Active"]  # idle before the load
+    rows += ["0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active"] * 5
+    rows += ["0, 1980, 2070, 1398.0, 0x4, Not Active, Not Active, Not Active, Active"]
+    rows += ["garbage line", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    with open(cs.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    cs.fh = open(cs.path)
+    cs.proc = _Done()
+    got = cs.stop()
+    assert got["sm_mhz"] == 2070.0 and got["sm_max_mhz"] == 2070.0
+    assert got["reasons"] == ["sw_power_cap"]
+    assert got["samples"] == 7
+    off = bench.ClockSampler(0)
+    assert off.stop()["reasons"] == ["nvidia-smi unavailable"]
