@@ -182,3 +182,17 @@ def test_library_filter_design_rejects_bad_input(lib):
         assert e.value.status == pfe.PFE_E_ARG
     m, c = pfe.pfe_design_filter("pq", -0.9, -0.8, eps=0.01, r=0.3, degree=60000)
     assert m == 60000 and c.size == 60001
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libpfe.so the binding raises: there is no CPU or eager fallback."""
+    import subprocess
+    import sys
+
+    code = ("import paper_1902_07041_gb300 as p\n"
+            "try:\n"
+            f"    p.load({str(tmp_path / 'libpfe.so')!r})\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'not built' in str(e))\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.stdout.strip() == "raised True", out.stderr
