@@ -196,3 +196,17 @@ def test_missing_library_fails_loudly(tmp_path):
             "    print('raised', 'not built' in str(e))\n")
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert out.stdout.strip() == "raised True", out.stderr
+
+
+def test_product_path_is_independent_of_the_oracle():
+    """The library, its binding and its build share nothing with the oracle: no import of it, no
+    include of its sources, no link against it, and nothing committed reads the scratch folder."""
+    pkg = os.path.join(ROOT, "paper_1902_07041_gb300")
+    bad = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)|#\s*include\s*[<\"][^>\"]*oracle|liboracle|[\"'/]_work/", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not bad.search(src), os.path.join(dirpath, f)
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        assert "oracle" not in open(os.path.join(ROOT, "include", f)).read().lower(), f
